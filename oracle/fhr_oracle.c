@@ -1,0 +1,567 @@
+/*
+ * FP64 CPU oracle for the fast hyperspectral reconstruction (FHR) path of
+ * "Fast Hyperspectral Neutron Tomography" (arXiv 2410.22500).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the FHR path computes.  It is called by the tests, by the
+ * smoke check and by the benchmark's CPU-baseline leg, and by nothing else.
+ * It shares no code, header, table or constant with the CUDA library.
+ *
+ * Everything is double precision, single threaded, written as plain loops in
+ * the order the paper states the steps.  Each function cites the passage it
+ * follows.  Where the paper is silent, the reading taken is stated beside the
+ * code (and listed with the design notes of the project).
+ *
+ * Layouts (row-major C arrays):
+ *   counts y   [Nv][Nr][Nc][Nk]      open beam y0 [Nr][Nc][Nk]
+ *   P          [Np][Nk], pixel j = (v*Nc + c)*Nr + r   (the paper's p, Np x Nk)
+ *   D          [Nk][K]   (the paper's D^s)              W [Np][K] (the paper's V^s)
+ *   volume x   [N][N][Wl], element (iy, ix, w), w = r*K + j (slice r, channel j)
+ *   sinogram   [Nv][Nc][Wl]  (equal to W viewed with Wl = Nr*K)
+ *   x^h        [Nr][N][N][Nk]
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_ERR_ARG -1
+#define OR_ERR_NOMEM -2
+
+static double dmax(double a, double b) { return a > b ? a : b; }
+static double dmin(double a, double b) { return a < b ? a : b; }
+
+/* ------------------------------------------------------------------------
+ * Normalisation.  Eq. (neglogattenuation): p = -log(y / y^o).
+ * Appendix A, Eq. (off_corr_proof)/(back_offset): with a background pixel set
+ * B, b_{v,k} = mean over (r,c) in B of -log(y/y^o), and p <- p - b.
+ * Readings (paper silent): counts are clamped at 1 before the log so zero
+ * counts stay finite; p is clamped at 0 afterwards because the factorisation
+ * of Eq. (sub_extract_solve) needs p >= 0; a dead wavelength bin (mask [Nk])
+ * gives p = 0 for every pixel.
+ * Output pixel order is (v, c, r) so that P's rows, read K at a time, are the
+ * subspace sinogram in [view][bin][slice] order.
+ * ---------------------------------------------------------------------- */
+int or_normalise(int Nv, int Nr, int Nc, int Nk,
+                 const uint16_t *y, const uint16_t *y0,
+                 const uint8_t *bg,   /* [Nr][Nc] or NULL */
+                 const uint8_t *dead, /* [Nk] or NULL */
+                 double *P,           /* [Nv*Nc*Nr][Nk] */
+                 double *b_out)       /* [Nv][Nk] or NULL */
+{
+    if (Nv <= 0 || Nr <= 0 || Nc <= 0 || Nk <= 0) return OR_ERR_ARG;
+    double *b = (double *)calloc((size_t)Nv * Nk, sizeof(double));
+    if (!b) return OR_ERR_NOMEM;
+    if (bg) {
+        long nb = 0;
+        for (int r = 0; r < Nr; ++r)
+            for (int c = 0; c < Nc; ++c) nb += bg[r * Nc + c] ? 1 : 0;
+        if (nb > 0) {
+            for (int v = 0; v < Nv; ++v)
+                for (int k = 0; k < Nk; ++k) {
+                    double s = 0.0;
+                    for (int r = 0; r < Nr; ++r)
+                        for (int c = 0; c < Nc; ++c) {
+                            if (!bg[r * Nc + c]) continue;
+                            double yy = y[(((size_t)v * Nr + r) * Nc + c) * Nk + k];
+                            double yo = y0[((size_t)r * Nc + c) * Nk + k];
+                            s += log(dmax(yo, 1.0)) - log(dmax(yy, 1.0));
+                        }
+                    b[(size_t)v * Nk + k] = s / (double)nb;
+                }
+        }
+    }
+    for (int v = 0; v < Nv; ++v)
+        for (int r = 0; r < Nr; ++r)
+            for (int c = 0; c < Nc; ++c) {
+                size_t j = ((size_t)v * Nc + c) * Nr + r;
+                for (int k = 0; k < Nk; ++k) {
+                    double yy = y[(((size_t)v * Nr + r) * Nc + c) * Nk + k];
+                    double yo = y0[((size_t)r * Nc + c) * Nk + k];
+                    double p = log(dmax(yo, 1.0)) - log(dmax(yy, 1.0));
+                    p -= b[(size_t)v * Nk + k];
+                    p = dmax(p, 0.0);
+                    if (dead && dead[k]) p = 0.0;
+                    P[j * Nk + k] = p;
+                }
+            }
+    if (b_out) memcpy(b_out, b, sizeof(double) * (size_t)Nv * Nk);
+    free(b);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Subspace extraction, Eq. (sub_extract_solve): min ||p - V D^T||_F^2 over
+ * V >= 0, D >= 0, solved (Sec. III) by coordinate descent with fast HALS
+ * updates.  Each half-step minimises the objective exactly over one
+ * coordinate at a time (a 1-D nonnegative quadratic), coordinates in natural
+ * order, Gauss-Seidel within a row:
+ *   V row j:  v_js <- max(0, v_js + ((p_j D)_s - sum_t (D^T D)_{s,t} v_jt) / (D^T D)_{s,s})
+ *   D row k:  d_ks <- max(0, d_ks + ((p^T V)_{k,s} - sum_t d_kt (V^T V)_{t,s}) / (V^T V)_{s,s})
+ * A coordinate whose Gram diagonal is zero is left unchanged.
+ * ---------------------------------------------------------------------- */
+void or_gram(long rows, int K, const double *X, double *G)
+{
+    for (int s = 0; s < K; ++s)
+        for (int t = 0; t < K; ++t) {
+            double a = 0.0;
+            for (long i = 0; i < rows; ++i) a += X[i * K + s] * X[i * K + t];
+            G[s * K + t] = a;
+        }
+}
+
+int or_hals_update_W(long Np, int Nk, int K, const double *P, const double *D, double *W)
+{
+    if (K <= 0 || K > 64) return OR_ERR_ARG;
+    double G[64 * 64], r[64];
+    or_gram(Nk, K, D, G);
+    for (long j = 0; j < Np; ++j) {
+        const double *p = P + j * Nk;
+        double *w = W + j * K;
+        for (int s = 0; s < K; ++s) {
+            double a = 0.0;
+            for (int k = 0; k < Nk; ++k) a += p[k] * D[(size_t)k * K + s];
+            r[s] = a;
+        }
+        for (int s = 0; s < K; ++s) {
+            double h = G[s * K + s];
+            if (h == 0.0) continue;
+            double g = r[s];
+            for (int t = 0; t < K; ++t) g -= G[s * K + t] * w[t];
+            w[s] = dmax(0.0, w[s] + g / h);
+        }
+    }
+    return OR_OK;
+}
+
+int or_hals_update_D(long Np, int Nk, int K, const double *P, const double *W, double *D)
+{
+    if (K <= 0 || K > 64) return OR_ERR_ARG;
+    double G[64 * 64];
+    or_gram(Np, K, W, G);
+    double *Q = (double *)calloc((size_t)Nk * K, sizeof(double));
+    if (!Q) return OR_ERR_NOMEM;
+    for (long j = 0; j < Np; ++j)
+        for (int k = 0; k < Nk; ++k) {
+            double p = P[j * Nk + k];
+            for (int s = 0; s < K; ++s) Q[(size_t)k * K + s] += p * W[j * K + s];
+        }
+    for (int k = 0; k < Nk; ++k) {
+        double *d = D + (size_t)k * K;
+        for (int s = 0; s < K; ++s) {
+            double h = G[s * K + s];
+            if (h == 0.0) continue;
+            double g = Q[(size_t)k * K + s];
+            for (int t = 0; t < K; ++t) g -= d[t] * G[t * K + s];
+            d[s] = dmax(0.0, d[s] + g / h);
+        }
+    }
+    free(Q);
+    return OR_OK;
+}
+
+/* Reading (paper silent): after each D half-step the columns of D are scaled
+ * to unit L2 norm and the matching columns of V by the inverse factor, so the
+ * product V D^T (and the objective) is unchanged.  Zero columns are kept. */
+void or_normalise_columns(long Np, int Nk, int K, double *D, double *W, double *norms)
+{
+    for (int s = 0; s < K; ++s) {
+        double a = 0.0;
+        for (int k = 0; k < Nk; ++k) a += D[(size_t)k * K + s] * D[(size_t)k * K + s];
+        double n = sqrt(a);
+        if (norms) norms[s] = n;
+        if (n > 0.0) {
+            for (int k = 0; k < Nk; ++k) D[(size_t)k * K + s] /= n;
+            for (long j = 0; j < Np; ++j) W[j * K + s] *= n;
+        }
+    }
+}
+
+/* ||p - V D^T||_F^2, evaluated entry by entry (Eq. sub_extract_solve, no 1/2). */
+double or_objective(long Np, int Nk, int K, const double *P, const double *D, const double *W)
+{
+    double f = 0.0;
+    for (long j = 0; j < Np; ++j)
+        for (int k = 0; k < Nk; ++k) {
+            double e = P[j * Nk + k];
+            for (int s = 0; s < K; ++s) e -= W[j * K + s] * D[(size_t)k * K + s];
+            f += e * e;
+        }
+    return f;
+}
+
+/* `iters` full iterations, each: V half-step, D half-step, column scaling,
+ * objective.  obj[t] (if non-NULL) receives the objective after iteration t. */
+int or_nmf(long Np, int Nk, int K, int iters, const double *P, double *D, double *W,
+           double *obj)
+{
+    for (int t = 0; t < iters; ++t) {
+        int e = or_hals_update_W(Np, Nk, K, P, D, W);
+        if (e) return e;
+        e = or_hals_update_D(Np, Nk, K, P, W, D);
+        if (e) return e;
+        or_normalise_columns(Np, Nk, K, D, W, NULL);
+        if (obj) obj[t] = or_objective(Np, Nk, K, P, D, W);
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Parallel-beam projector A of Eq. (porj_matd_rel) / Eq. (recon).  The paper
+ * does not state its discretisation (it uses a library).  Reading: the strip
+ * (area) model.  A_{(v,c),i} = area(pixel_i  intersect  strip_{v,c}) / du, with
+ * strip_{v,c} = {(x,y): |x cos t_v + y sin t_v - u_c| <= du/2}, unit pixels and
+ * unit bins (du = 1).  Two independent constructions are given: the closed
+ * form below (integral of the pixel's trapezoidal footprint over the bin) and
+ * polygon clipping (or_strip_area_polyclip) for brute-force checks.
+ * ---------------------------------------------------------------------- */
+
+/* Cumulative integral of the footprint of a unit square seen at direction
+ * (cos t, sin t): the footprint is a trapezoid of total area 1, flat top of
+ * height 1/hi for |s| <= (hi-lo)/2, linear to 0 at |s| = (hi+lo)/2, where
+ * hi = max(|cos|,|sin|), lo = min(|cos|,|sin|). */
+static double footprint_cdf(double s, double hi, double lo)
+{
+    double t2 = 0.5 * (hi + lo), t1 = 0.5 * (hi - lo);
+    if (s <= -t2) return 0.0;
+    if (s >= t2) return 1.0;
+    if (s <= -t1) return (s + t2) * (s + t2) / (2.0 * hi * lo);
+    if (s <= t1) return lo / (2.0 * hi) + (s + t1) / hi;
+    return 1.0 - (t2 - s) * (t2 - s) / (2.0 * hi * lo);
+}
+
+double or_strip_area(double theta, double px, double py, double uc)
+{
+    double c = cos(theta), s = sin(theta);
+    double a = fabs(c), b = fabs(s);
+    double hi = dmax(a, b), lo = dmin(a, b);
+    double u0 = px * c + py * s;
+    return footprint_cdf(uc + 0.5 - u0, hi, lo) - footprint_cdf(uc - 0.5 - u0, hi, lo);
+}
+
+/* Sutherland-Hodgman clipping of a convex polygon by the half-plane
+ * nx*x + ny*y <= d.  Returns the new vertex count. */
+static int clip_halfplane(const double *in, int n, double nx, double ny, double d, double *out)
+{
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        const double *P = in + 2 * i, *Q = in + 2 * ((i + 1) % n);
+        double fp = nx * P[0] + ny * P[1] - d, fq = nx * Q[0] + ny * Q[1] - d;
+        if (fp <= 0) { out[2 * m] = P[0]; out[2 * m + 1] = P[1]; ++m; }
+        if ((fp < 0 && fq > 0) || (fp > 0 && fq < 0)) {
+            double tt = fp / (fp - fq);
+            out[2 * m] = P[0] + tt * (Q[0] - P[0]);
+            out[2 * m + 1] = P[1] + tt * (Q[1] - P[1]);
+            ++m;
+        }
+    }
+    return m;
+}
+
+double or_strip_area_polyclip(double theta, double px, double py, double uc)
+{
+    double A[32], B[32];
+    double c = cos(theta), s = sin(theta);
+    A[0] = px - 0.5; A[1] = py - 0.5;
+    A[2] = px + 0.5; A[3] = py - 0.5;
+    A[4] = px + 0.5; A[5] = py + 0.5;
+    A[6] = px - 0.5; A[7] = py + 0.5;
+    int n = clip_halfplane(A, 4, c, s, uc + 0.5, B);          /* u <= uc + 1/2 */
+    n = clip_halfplane(B, n, -c, -s, -(uc - 0.5), A);          /* u >= uc - 1/2 */
+    double area = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double *P = A + 2 * i, *Q = A + 2 * ((i + 1) % n);
+        area += P[0] * Q[1] - Q[0] * P[1];
+    }
+    return 0.5 * fabs(area);
+}
+
+static double pix_x(int ix, int N) { return ix - 0.5 * (N - 1); }
+static double bin_u(int c, int Nc) { return c - 0.5 * (Nc - 1); }
+
+/* Dense system matrix [Nv*Nc][N*N] (tiny cases only). */
+void or_system_matrix(int N, int Nc, int Nv, const double *theta, int polyclip, double *A)
+{
+    for (int v = 0; v < Nv; ++v)
+        for (int c = 0; c < Nc; ++c)
+            for (int iy = 0; iy < N; ++iy)
+                for (int ix = 0; ix < N; ++ix) {
+                    double px = pix_x(ix, N), py = pix_x(iy, N), uc = bin_u(c, Nc);
+                    A[((size_t)v * Nc + c) * N * N + (size_t)iy * N + ix] =
+                        polyclip ? or_strip_area_polyclip(theta[v], px, py, uc)
+                                 : or_strip_area(theta[v], px, py, uc);
+                }
+}
+
+/* The bins a pixel's footprint can touch at angle theta: every c whose strip
+ * centre lies within 1/2 + (|cos|+|sin|)/2 of the pixel's projected centre.
+ * Outside that range the strip area is exactly zero. */
+static void bin_range(double theta, double px, double py, int Nc, int *c0, int *c1)
+{
+    double c = cos(theta), s = sin(theta);
+    double u0 = px * c + py * s;
+    double half = 0.5 + 0.5 * (fabs(c) + fabs(s));
+    double lo = u0 - half + 0.5 * (Nc - 1), hi = u0 + half + 0.5 * (Nc - 1);
+    int a = (int)floor(lo), b = (int)ceil(hi);
+    if (a < 0) a = 0;
+    if (b > Nc - 1) b = Nc - 1;
+    *c0 = a;
+    *c1 = b;
+}
+
+/* y = A x over a vector of Wl values per pixel / per ray. */
+void or_project(int N, int Nc, int Nv, const double *theta, int Wl, const double *x, double *y)
+{
+    memset(y, 0, sizeof(double) * (size_t)Nv * Nc * Wl);
+    for (int v = 0; v < Nv; ++v)
+        for (int iy = 0; iy < N; ++iy)
+            for (int ix = 0; ix < N; ++ix) {
+                double px = pix_x(ix, N), py = pix_x(iy, N);
+                int c0, c1;
+                bin_range(theta[v], px, py, Nc, &c0, &c1);
+                const double *xi = x + ((size_t)iy * N + ix) * Wl;
+                for (int c = c0; c <= c1; ++c) {
+                    double a = or_strip_area(theta[v], px, py, bin_u(c, Nc));
+                    if (a == 0.0) continue;
+                    double *yr = y + ((size_t)v * Nc + c) * Wl;
+                    for (int w = 0; w < Wl; ++w) yr[w] += a * xi[w];
+                }
+            }
+}
+
+/* x = A^T y (the exact transpose of or_project). */
+void or_backproject(int N, int Nc, int Nv, const double *theta, int Wl, const double *y, double *x)
+{
+    memset(x, 0, sizeof(double) * (size_t)N * N * Wl);
+    for (int v = 0; v < Nv; ++v)
+        for (int iy = 0; iy < N; ++iy)
+            for (int ix = 0; ix < N; ++ix) {
+                double px = pix_x(ix, N), py = pix_x(iy, N);
+                int c0, c1;
+                bin_range(theta[v], px, py, Nc, &c0, &c1);
+                double *xi = x + ((size_t)iy * N + ix) * Wl;
+                for (int c = c0; c <= c1; ++c) {
+                    double a = or_strip_area(theta[v], px, py, bin_u(c, Nc));
+                    if (a == 0.0) continue;
+                    const double *yr = y + ((size_t)v * Nc + c) * Wl;
+                    for (int w = 0; w < Wl; ++w) xi[w] += a * yr[w];
+                }
+            }
+}
+
+/* ------------------------------------------------------------------------
+ * MBIR reconstruction of each subspace channel, Eq. (recon):
+ *   x_j = argmin_x  1/(2 sigma_v^2) ||V_j - A x||^2 + h(x),
+ * with the qGGMRF prior h (Sec. III; the paper gives no formula, it cites the
+ * standard qGGMRF form):
+ *   h(x) = sum over neighbour pairs {s,r} of b_sr rho(x_s - x_r),
+ *   rho(d) = |d|^p / (p sigma_x^p) * u / (1 + u),  u = |d / (T sigma_x)|^(q-p).
+ * Readings (paper silent; its solver is a library): solved by separable
+ * quadratic surrogates (SQS) with the symmetric-bound surrogate of rho, so
+ * every iteration decreases the cost; x >= 0 enforced by clamping; q = 2;
+ * 8 in-plane neighbours (weight 1 edge, 1/sqrt2 diagonal) and 2 inter-slice
+ * neighbours (weight 1) when Nr > 1, all weights divided by their sum;
+ * voxels outside the volume are not neighbours.  `beta` scales h (1 = Eq.
+ * recon; 0 removes the prior, used by tests).
+ * Optional momentum: FISTA-style extrapolation of the SQS iterates.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    double p, q, T, beta;
+    int iters;
+    int momentum;
+} or_mbir_params;
+
+/* rho(d) */
+double or_qggmrf_rho(double d, double sx, double p, double q, double T)
+{
+    double a = fabs(d);
+    double u = pow(a / (T * sx), q - p);
+    return pow(a, p) / (p * pow(sx, p)) * u / (1.0 + u);
+}
+
+/* rho'(d)/d (the surrogate's half-curvature), finite at d = 0 for q = 2. */
+double or_qggmrf_influence(double d, double sx, double p, double q, double T)
+{
+    double a = fabs(d);
+    double u = pow(a / (T * sx), q - p);
+    double lead = pow(a, q - 2.0) / (pow(sx, p) * pow(T * sx, q - p));
+    return lead / (1.0 + u) * (1.0 + (q - p) / (p * (1.0 + u)));
+}
+
+/* neighbour offsets (dy, dx, dr) and raw weights */
+static const int NB_OFF[10][3] = {
+    {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0},
+    {-1, -1, 0}, {-1, 1, 0}, {1, -1, 0}, {1, 1, 0},
+    {0, 0, -1}, {0, 0, 1}};
+
+static void nb_weights(int Nr, double *bw, int *nnb)
+{
+    int n = Nr > 1 ? 10 : 8;
+    double r2 = 1.0 / sqrt(2.0), z = 0.0;
+    for (int i = 0; i < n; ++i) {
+        bw[i] = (i >= 4 && i < 8) ? r2 : 1.0;
+        z += bw[i];
+    }
+    for (int i = 0; i < n; ++i) bw[i] /= z;
+    *nnb = n;
+}
+
+/* Cost of Eq. (recon) summed over channels: sum_j [ ||V_j - A x_j||^2 / (2 sv_j^2) + beta h_j(x_j) ]. */
+double or_mbir_cost(int N, int Nr, int K, int Nc, int Nv, const double *theta, const double *V,
+                    const double *sv, const double *sx, const or_mbir_params *prm, const double *x)
+{
+    int Wl = Nr * K;
+    double *Ax = (double *)malloc(sizeof(double) * (size_t)Nv * Nc * Wl);
+    if (!Ax) return NAN;
+    or_project(N, Nc, Nv, theta, Wl, x, Ax);
+    double f = 0.0;
+    for (size_t i = 0; i < (size_t)Nv * Nc; ++i)
+        for (int w = 0; w < Wl; ++w) {
+            double e = V[i * Wl + w] - Ax[i * Wl + w];
+            double s = sv[w % K];
+            f += e * e / (2.0 * s * s);
+        }
+    free(Ax);
+    double bw[10];
+    int nnb;
+    nb_weights(Nr, bw, &nnb);
+    /* each unordered pair once: only the "forward" half of the offsets */
+    const int fwd[5] = {1, 3, 6, 7, 9};
+    for (int iy = 0; iy < N; ++iy)
+        for (int ix = 0; ix < N; ++ix)
+            for (int r = 0; r < Nr; ++r)
+                for (int j = 0; j < K; ++j) {
+                    double xs = x[((size_t)iy * N + ix) * Wl + r * K + j];
+                    for (int q = 0; q < 5; ++q) {
+                        int o = fwd[q];
+                        if (o >= nnb) continue;
+                        int yy = iy + NB_OFF[o][0], xx = ix + NB_OFF[o][1], rr = r + NB_OFF[o][2];
+                        if (yy < 0 || yy >= N || xx < 0 || xx >= N || rr < 0 || rr >= Nr) continue;
+                        double xr = x[((size_t)yy * N + xx) * Wl + rr * K + j];
+                        f += prm->beta * bw[o] * or_qggmrf_rho(xs - xr, sx[j], prm->p, prm->q, prm->T);
+                    }
+                }
+    return f;
+}
+
+/* One SQS step from z: returns x_new (may alias nothing). dA = A^T A 1 per pixel. */
+static void sqs_step(int N, int Nr, int K, int Nc, int Nv, const double *theta, const double *V,
+                     const double *sv, const double *sx, const or_mbir_params *prm,
+                     const double *dA, const double *z, double *xnew, double *e, double *bp)
+{
+    int Wl = Nr * K;
+    or_project(N, Nc, Nv, theta, Wl, z, e);
+    for (size_t i = 0; i < (size_t)Nv * Nc * Wl; ++i) e[i] = V[i] - e[i];
+    or_backproject(N, Nc, Nv, theta, Wl, e, bp);
+    double bw[10];
+    int nnb;
+    nb_weights(Nr, bw, &nnb);
+    for (int iy = 0; iy < N; ++iy)
+        for (int ix = 0; ix < N; ++ix)
+            for (int r = 0; r < Nr; ++r)
+                for (int j = 0; j < K; ++j) {
+                    size_t idx = ((size_t)iy * N + ix) * Wl + r * K + j;
+                    double s2 = sv[j] * sv[j];
+                    double g = -bp[idx] / s2;
+                    double d = dA[(size_t)iy * N + ix] / s2;
+                    if (prm->beta != 0.0) {
+                        for (int o = 0; o < nnb; ++o) {
+                            int yy = iy + NB_OFF[o][0], xx = ix + NB_OFF[o][1], rr = r + NB_OFF[o][2];
+                            if (yy < 0 || yy >= N || xx < 0 || xx >= N || rr < 0 || rr >= Nr) continue;
+                            double dl = z[idx] - z[((size_t)yy * N + xx) * Wl + rr * K + j];
+                            double wt = or_qggmrf_influence(dl, sx[j], prm->p, prm->q, prm->T);
+                            g += prm->beta * bw[o] * dl * wt;
+                            d += 2.0 * prm->beta * bw[o] * wt;
+                        }
+                    }
+                    xnew[idx] = d > 0.0 ? dmax(0.0, z[idx] - g / d) : z[idx];
+                }
+}
+
+int or_mbir(int N, int Nr, int K, int Nc, int Nv, const double *theta, const double *V,
+            const double *sv, const double *sx, const or_mbir_params *prm, double *x,
+            double *cost_hist)
+{
+    if (N <= 0 || Nr <= 0 || K <= 0 || Nc <= 0 || Nv <= 0 || !prm) return OR_ERR_ARG;
+    int Wl = Nr * K;
+    size_t nx = (size_t)N * N * Wl, ny = (size_t)Nv * Nc * Wl;
+    double *dA = (double *)malloc(sizeof(double) * (size_t)N * N);
+    double *ones = (double *)malloc(sizeof(double) * (size_t)N * N);
+    double *A1 = (double *)malloc(sizeof(double) * (size_t)Nv * Nc);
+    double *e = (double *)malloc(sizeof(double) * ny);
+    double *bp = (double *)malloc(sizeof(double) * nx);
+    double *xn = (double *)malloc(sizeof(double) * nx);
+    double *z = (double *)malloc(sizeof(double) * nx);
+    if (!dA || !ones || !A1 || !e || !bp || !xn || !z) {
+        free(dA); free(ones); free(A1); free(e); free(bp); free(xn); free(z);
+        return OR_ERR_NOMEM;
+    }
+    for (size_t i = 0; i < (size_t)N * N; ++i) ones[i] = 1.0;
+    or_project(N, Nc, Nv, theta, 1, ones, A1);
+    or_backproject(N, Nc, Nv, theta, 1, A1, dA);
+    memcpy(z, x, sizeof(double) * nx);
+    double t = 1.0;
+    for (int it = 0; it < prm->iters; ++it) {
+        sqs_step(N, Nr, K, Nc, Nv, theta, V, sv, sx, prm, dA, z, xn, e, bp);
+        if (prm->momentum) {
+            double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+            double a = (t - 1.0) / tn;
+            for (size_t i = 0; i < nx; ++i) {
+                double zn = xn[i] + a * (xn[i] - x[i]);
+                z[i] = dmax(zn, 0.0);
+                x[i] = xn[i];
+            }
+            t = tn;
+        } else {
+            memcpy(x, xn, sizeof(double) * nx);
+            memcpy(z, xn, sizeof(double) * nx);
+        }
+        if (cost_hist) cost_hist[it] = or_mbir_cost(N, Nr, K, Nc, Nv, theta, V, sv, sx, prm, x);
+    }
+    free(dA); free(ones); free(A1); free(e); free(bp); free(xn); free(z);
+    return OR_OK;
+}
+
+/* Reading (paper silent on sigma_v, sigma_x): per channel j, from the
+ * channel's sinogram V_j over all views, bins and slices:
+ *   sigma_v = rms(V_j) * 10^(-snr_db/20),   sigma_x = 0.2 * mean(V_j) / Nc.
+ * A channel whose sinogram is all zero gets sigma_v = sigma_x = 1. */
+void or_mbir_sigmas(long rows, int K, const double *V, double snr_db, int Nc, double *sv, double *sx)
+{
+    for (int j = 0; j < K; ++j) {
+        double s1 = 0.0, s2 = 0.0;
+        for (long i = 0; i < rows; ++i) {
+            double v = V[i * K + j];
+            s1 += v;
+            s2 += v * v;
+        }
+        double rms = sqrt(s2 / (double)rows), mean = s1 / (double)rows;
+        if (rms > 0.0 && mean > 0.0) {
+            sv[j] = rms * pow(10.0, -snr_db / 20.0);
+            sx[j] = 0.2 * mean / (double)Nc;
+        } else {
+            sv[j] = 1.0;
+            sx[j] = 1.0;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Subspace expansion, Eq. (sub_expansion): x^h = x^s (D^s)^T.
+ * xs [N][N][Nr*K] (iy, ix, r*K+j) -> xh [Nr][N][N][Nk].
+ * ---------------------------------------------------------------------- */
+void or_expand(int N, int Nr, int K, int Nk, const double *xs, const double *D, double *xh)
+{
+    for (int r = 0; r < Nr; ++r)
+        for (int iy = 0; iy < N; ++iy)
+            for (int ix = 0; ix < N; ++ix) {
+                const double *a = xs + ((size_t)iy * N + ix) * Nr * K + (size_t)r * K;
+                double *o = xh + (((size_t)r * N + iy) * N + ix) * Nk;
+                for (int k = 0; k < Nk; ++k) {
+                    double s = 0.0;
+                    for (int j = 0; j < K; ++j) s += a[j] * D[(size_t)k * K + j];
+                    o[k] = s;
+                }
+            }
+}
