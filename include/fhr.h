@@ -1,0 +1,235 @@
+/*
+ * fhr.h -- C ABI of libfhr, a GB300 (sm_103a) implementation of the fast
+ * hyperspectral reconstruction (FHR) path of "Fast Hyperspectral Neutron
+ * Tomography" (Chowdhury et al., arXiv 2410.22500), Algorithm 1:
+ *
+ *   counts y, open beam y0 --normalise--> p --decompose--> (V^s, D^s)
+ *   --reconstruct--> x^s --expand--> x^h
+ *
+ * Conventions shared by every entry point
+ *   - Array arguments are DEVICE pointers owned by the caller, unless an entry
+ *     point says otherwise.  The library never allocates device memory: calls
+ *     that need scratch take a caller-provided workspace whose size is
+ *     returned by the matching *_workspace_size function (256-byte aligned).
+ *   - Every call is asynchronous on the stream of the context (fhr_create /
+ *     fhr_set_stream).  Inputs must stay valid and outputs must not be read
+ *     until the stream reaches the call.
+ *   - Errors: a negative fhr_status.  Argument errors are found on the host
+ *     before anything is launched; fhr_last_error() describes the last one.
+ *     Errors found on the device (a bounded wait that expired, a non-finite
+ *     objective) are written to a status word inside the workspace and
+ *     returned by fhr_workspace_status() after a stream synchronisation.
+ *     No kernel of this library traps.
+ *   - Sizes are element counts; strides are in elements.
+ *
+ * Notation (paper Sec. II): Nv views, Nr detector rows (= volume slices),
+ * Nc detector columns, Nk wavelength bins, Np = Nv*Nr*Nc projections,
+ * K = N_s subspace dimension, N x N image per slice.
+ *
+ * Layouts
+ *   y   [Nv][Nr][Nc][Nk] uint16     y0 [Nr][Nc][Nk] uint16
+ *   P   [Np][ldP], row j = (v*Nc + c)*Nr + r, padding columns Nk..ldP-1 zero
+ *   D   [Nk][K] float (the paper's D^s)
+ *   W   [Np][K] float (the paper's V^s); viewed as [Nv][Nc][Nr*K] it is the
+ *       subspace sinogram, channel index w = r*K + j
+ *   xs  [N][N][Nr*K] float (the paper's x^s, slice and channel innermost)
+ *   xh  [Nr][N][N][Nk] float or bf16 (the paper's x^h)
+ * Geometry: unit pixels centred on the origin, pixel (iy, ix) at
+ * (ix - (N-1)/2, iy - (N-1)/2); unit detector bins at u_c = c - (Nc-1)/2;
+ * default angles theta_v = v*pi/Nv.
+ */
+#ifndef FHR_H
+#define FHR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fhr_status;
+#define FHR_OK 0
+#define FHR_ERR_ARG (-1)         /* invalid argument: null pointer, size, alignment, workspace too small */
+#define FHR_ERR_CUDA (-2)        /* a CUDA runtime call failed (message in fhr_last_error) */
+#define FHR_ERR_TIMEOUT (-3)     /* a device-side bounded wait expired; the kernel returned early */
+#define FHR_ERR_NONFINITE (-4)   /* a non-finite value reached an objective or Gram reduction */
+#define FHR_ERR_UNSUPPORTED (-5) /* parameter combination not implemented (e.g. K > 8, q != 2) */
+
+#define FHR_F32 0
+#define FHR_BF16 1
+
+typedef struct fhr_ctx fhr_ctx;
+
+/* Context: device ordinal and stream (a cudaStream_t, NULL = legacy default).
+ * Holds only host state (device properties, last error text). */
+fhr_status fhr_create(fhr_ctx **ctx, int device, void *stream);
+void fhr_destroy(fhr_ctx *ctx);
+fhr_status fhr_set_stream(fhr_ctx *ctx, void *stream);
+const char *fhr_last_error(const fhr_ctx *ctx);
+const char *fhr_version(void);
+
+/* Launch accounting (for benchmarks; not part of Algorithm 1).  Every kernel
+ * launch made through a context is counted.  fhr_profile_enable(ctx, 1)
+ * resets the counters and, until disabled, brackets each launch of the timed
+ * kernel families with CUDA events on the context's stream (host-side event
+ * objects; no device memory).  fhr_profile_read(ctx, name, ...) synchronises
+ * those events and returns the number of launches and their summed device
+ * time in ms for `name` in {"normalise", "nmf_pass", "nmf_reduce",
+ * "nmf_update", "proj_fwd", "mbir_update", "proj_bwd", "expand"}; with
+ * name == NULL it returns the total launch count since the last enable. */
+fhr_status fhr_profile_enable(fhr_ctx *ctx, int enable);
+fhr_status fhr_profile_read(fhr_ctx *ctx, const char *name, long long *launches, double *ms);
+
+/* Device status word kept at the start of every workspace (FHR_OK or a
+ * negative code).  Synchronises the context's stream, reads it, and clears it. */
+fhr_status fhr_workspace_status(fhr_ctx *ctx, void *ws);
+
+/* ------------------------------------------------------------------------
+ * Normalisation -- Eq. (neglogattenuation), p = -log(y / y0), with the
+ * offset correction of Appendix A, Eq. (back_offset): when bg_mask is given,
+ * b_{v,k} = mean over background pixels of -log(y/y0) and p <- p - b.
+ * Readings of points the paper leaves open: counts are clamped at 1 before
+ * the logarithm; p is clamped at 0 afterwards (NMF needs p >= 0); bins with
+ * dead_bins[k] != 0 give p = 0.
+ *   y, y0      counts (layouts above)
+ *   bg_mask    [Nr][Nc] uint8 or NULL; b_out [Nv][Nk] float receives b and
+ *              is required when bg_mask is given (else may be NULL)
+ *   dead_bins  [Nk] uint8 or NULL
+ *   P          output [Np][ldP], FHR_F32 (ldP % 4 == 0) or FHR_BF16 (ldP % 8 == 0)
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int Nv, Nr, Nc, Nk;
+    int ldP;       /* >= Nk */
+    int p_dtype;   /* FHR_F32 or FHR_BF16 */
+} fhr_norm_params;
+
+fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *prm,
+                         const uint16_t *y, const uint16_t *y0,
+                         const uint8_t *bg_mask, const uint8_t *dead_bins,
+                         float *b_out, void *P);
+
+/* ------------------------------------------------------------------------
+ * Subspace decomposition -- Eq. (sub_extract_solve), min ||p - V D^T||_F^2
+ * over V >= 0, D >= 0, by fast-HALS coordinate descent (Sec. III).  One
+ * iteration: V half-step (Gauss-Seidel over the K coordinates of each
+ * pixel), D half-step, then the columns of D are scaled to unit L2 norm
+ * and V's columns by the inverse factor (the product is unchanged).  The
+ * V half-step, D^T p and p V^T are one fused pass that reads P once.
+ *   init  FHR_INIT_GIVEN: D, W hold the starting point on entry.
+ *         FHR_INIT_NNDSVD: NNDSVD start (Sec. III) from a randomised
+ *         subspace iteration for the top-K singular vectors of P, seeded
+ *         by `seed` (counter-based generator, splitmix64).
+ *   P     [Np][ldP] in p_dtype; D [Nk][K] and W [Np][K] float, in/out.
+ *   obj   device double [iters] or NULL: ||p - V D^T||^2 after each
+ *         iteration, from the Gram identity in double precision.
+ * K must be 1..8.  Nk <= 8192.
+ * ---------------------------------------------------------------------- */
+#define FHR_INIT_GIVEN 0
+#define FHR_INIT_NNDSVD 1
+
+typedef struct {
+    int64_t Np;
+    int Nk, ldP, K;
+    int iters;
+    int init;
+    int p_dtype;
+    int power_iters;   /* subspace iterations for NNDSVD (default 12 when 0) */
+    uint64_t seed;
+} fhr_nmf_params;
+
+fhr_status fhr_decompose_workspace_size(fhr_ctx *ctx, const fhr_nmf_params *prm, size_t *bytes);
+fhr_status fhr_decompose(fhr_ctx *ctx, const fhr_nmf_params *prm, const void *P,
+                         float *D, float *W, double *obj, void *ws, size_t ws_bytes);
+
+/* ------------------------------------------------------------------------
+ * Parallel-beam projector of Eq. (porj_matd_rel)/(recon): the strip-area
+ * model A_{(v,c),i} = area(pixel i intersect strip of bin c at view v).
+ * The weights are computed once per call in double precision into two
+ * tables (one per direction), so the back projector is the exact transpose
+ * of the forward one.  Both act on Wl values per pixel / per ray:
+ *   fhr_project:     y[v][c][w] = sum_i A x[i][w]     (x [N][N][Wl], y [Nv][Nc][Wl])
+ *   fhr_backproject: x[i][w]    = sum_(v,c) A y[v][c][w]
+ * angles: device double [Nv] radians, or NULL for v*pi/Nv.
+ * N >= 4, Nc >= 3.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int N, Nr, Nc, Nv;
+    const double *angles;
+} fhr_geom;
+
+fhr_status fhr_projector_workspace_size(fhr_ctx *ctx, const fhr_geom *g, size_t *bytes);
+fhr_status fhr_project(fhr_ctx *ctx, const fhr_geom *g, int Wl, const float *x, float *y,
+                       void *ws, size_t ws_bytes);
+fhr_status fhr_backproject(fhr_ctx *ctx, const fhr_geom *g, int Wl, const float *y, float *x,
+                           void *ws, size_t ws_bytes);
+
+/* ------------------------------------------------------------------------
+ * MBIR of every subspace channel, Eq. (recon):
+ *   x_j = argmin 1/(2 sigma_v^2) ||V_j - A x_j||^2 + beta * h(x_j),
+ * h the qGGMRF prior rho(d) = |d|^p/(p sx^p) * u/(1+u), u = |d/(T sx)|^(q-p),
+ * over 8 in-plane neighbours (weights 1 edge, 1/sqrt2 diagonal) and, when
+ * Nr > 1, 2 inter-slice neighbours (weight 1), weights divided by their sum.
+ * Solved by separable quadratic surrogates (monotone), x >= 0, optionally
+ * with momentum.  All Nr slices and K channels in one pass per iteration.
+ *   sino   [Nv][Nc][Nr*K] (= W from fhr_decompose)
+ *   xs     [N][N][Nr*K], in: starting point, out: result
+ *   sigma_v, sigma_x: host float [K] or NULL; when NULL, per channel
+ *   sigma_v = rms(V_j) 10^(-snr_db/20), sigma_x = 0.2 mean(V_j) / Nc.
+ * q must be 2; 1 <= p <= 2.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int K;
+    int iters;
+    float p, q, T, beta;
+    float snr_db;
+    int momentum;
+    const float *sigma_v;
+    const float *sigma_x;
+} fhr_mbir_params;
+
+fhr_status fhr_reconstruct_workspace_size(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_params *prm,
+                                          size_t *bytes);
+fhr_status fhr_reconstruct(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_params *prm,
+                           const float *sino, float *xs, void *ws, size_t ws_bytes);
+
+/* ------------------------------------------------------------------------
+ * Subspace expansion -- Eq. (sub_expansion), x^h = x^s (D^s)^T.
+ *   xs [N][N][Nr*K] float, D [Nk][K] float -> xh [Nr][N][N][Nk] in xh_dtype.
+ * Bins k0..k1-1 only are written when 0 <= k0 < k1 <= Nk (a wavelength
+ * slab, stored as [Nr][N][N][k1-k0]); k0 = k1 = 0 means all bins.
+ * ---------------------------------------------------------------------- */
+fhr_status fhr_expand(fhr_ctx *ctx, int N, int Nr, int K, int Nk, int k0, int k1,
+                      const float *xs, const float *D, int xh_dtype, void *xh);
+
+/* ------------------------------------------------------------------------
+ * Algorithm 1 end to end: normalise -> decompose -> reconstruct -> expand.
+ * With host_io = 0, y, y0 and xh are device pointers.  With host_io = 1 they
+ * are HOST pointers: the counts are copied in and x^h copied out through
+ * staging buffers in the workspace, with asynchronous copies on the
+ * context's stream (pinned host memory makes them truly asynchronous).
+ * bg_mask, dead_bins are device pointers or NULL.  D_out [Nk][K] device
+ * float, obj device double [nmf.iters] or NULL.  nmf.init must be
+ * FHR_INIT_NNDSVD (the pipeline has no starting point of its own).  The
+ * reconstruction starts from x^s = 0.  Sizes in norm, nmf, geom and mbir
+ * must agree (Np = Nv*Nr*Nc, geom.Nr = norm.Nr, mbir.K = nmf.K).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    fhr_norm_params norm;
+    fhr_nmf_params nmf;
+    fhr_geom geom;
+    fhr_mbir_params mbir;
+    int xh_dtype;
+    int host_io;
+} fhr_pipeline_params;
+
+fhr_status fhr_pipeline_workspace_size(fhr_ctx *ctx, const fhr_pipeline_params *prm, size_t *bytes);
+fhr_status fhr_pipeline(fhr_ctx *ctx, const fhr_pipeline_params *prm,
+                        const uint16_t *y, const uint16_t *y0,
+                        const uint8_t *bg_mask, const uint8_t *dead_bins,
+                        float *D_out, void *xh, double *obj, void *ws, size_t ws_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FHR_H */

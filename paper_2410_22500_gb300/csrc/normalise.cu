@@ -1,0 +1,154 @@
+// Count normalisation: Eq. (neglogattenuation) with the offset correction of
+// Appendix A (Eq. back_offset).  HBM-bound: 2 bytes of counts in, 4 (f32) or
+// 2 (bf16) bytes of P out per element; the open beam is re-read from L2.
+#include "common.cuh"
+
+namespace fhr {
+
+// -log(y / y0) with counts clamped at 1: log of the correctly rounded ratio,
+// so the absolute error stays near one ulp of the result even when p is small.
+__device__ __forceinline__ float neglog_ratio(float y, float y0) {
+    return logf(__fdiv_rn(fmaxf(y0, 1.f), fmaxf(y, 1.f)));
+}
+
+// b[v][k] = mean over background pixels (r, c) of -log(y/y0); compensated sum.
+__global__ void offset_reduce_kernel(const uint16_t *y, const uint16_t *y0, const uint8_t *bg, int Nv, int Nr,
+                                     int Nc, int Nk, float *b) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.y;
+    if (k >= Nk) return;
+    float s = 0.f, comp = 0.f;
+    int nb = 0;
+    for (int r = 0; r < Nr; ++r)
+        for (int c = 0; c < Nc; ++c) {
+            if (!bg[r * Nc + c]) continue;
+            ++nb;
+            const float yy = y[(((size_t)v * Nr + r) * Nc + c) * Nk + k];
+            const float yo = y0[((size_t)r * Nc + c) * Nk + k];
+            const float x = neglog_ratio(yy, yo) - comp;
+            const float t = s + x;
+            comp = (t - s) - x;
+            s = t;
+        }
+    b[(size_t)v * Nk + k] = nb > 0 ? s / (float)nb : 0.f;
+}
+
+template <typename TO>
+__device__ __forceinline__ void store8(TO *dst, const float *p);
+template <>
+__device__ __forceinline__ void store8<float>(float *dst, const float *p) {
+    reinterpret_cast<float4 *>(dst)[0] = make_float4(p[0], p[1], p[2], p[3]);
+    reinterpret_cast<float4 *>(dst)[1] = make_float4(p[4], p[5], p[6], p[7]);
+}
+template <>
+__device__ __forceinline__ void store8<__nv_bfloat16>(__nv_bfloat16 *dst, const float *p) {
+    uint32_t u[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(p[2 * i], p[2 * i + 1]);
+        u[i] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(u[0], u[1], u[2], u[3]);
+}
+template <typename TO>
+__device__ __forceinline__ void store1(TO *dst, float p);
+template <>
+__device__ __forceinline__ void store1<float>(float *dst, float p) { *dst = p; }
+template <>
+__device__ __forceinline__ void store1<__nv_bfloat16>(__nv_bfloat16 *dst, float p) { *dst = __float2bfloat16_rn(p); }
+
+// One thread per (output pixel row j, chunk of 8 bins).  Output row j = (v*Nc + c)*Nr + r.
+// VEC: counts rows are 16-byte aligned (Nk % 8 == 0), 8 counts per 16-byte load.
+template <bool VEC, typename TO>
+__global__ void __launch_bounds__(256) normalise_kernel(const uint16_t *__restrict__ y, const uint16_t *__restrict__ y0,
+                                                        const uint8_t *__restrict__ dead, const float *__restrict__ b,
+                                                        int Nv, int Nr, int Nc, int Nk, int ldP, TO *__restrict__ P) {
+    const int nch = (ldP + 7) / 8;
+    const int64_t total = (int64_t)Nv * Nc * Nr * nch;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = idx / nch;
+        const int ch = (int)(idx - j * nch);
+        const int r = (int)(j % Nr);
+        const int64_t vc = j / Nr;
+        const int c = (int)(vc % Nc);
+        const int v = (int)(vc / Nc);
+        const uint16_t *yr = y + (((size_t)v * Nr + r) * Nc + c) * Nk;
+        const uint16_t *y0r = y0 + ((size_t)r * Nc + c) * Nk;
+        const int k0 = ch * 8;
+        float p[8];
+        if (VEC && k0 + 8 <= Nk) {
+            const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(yr + k0));
+            const uint4 o = __ldg(reinterpret_cast<const uint4 *>(y0r + k0));
+            const uint32_t aa[4] = {a.x, a.y, a.z, a.w}, oo[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                p[2 * i] = neglog_ratio((float)(aa[i] & 0xffffu), (float)(oo[i] & 0xffffu));
+                p[2 * i + 1] = neglog_ratio((float)(aa[i] >> 16), (float)(oo[i] >> 16));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = k0 + i;
+                p[i] = k < Nk ? neglog_ratio((float)yr[k], (float)y0r[k]) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = k0 + i;
+            float q = p[i];
+            if (b && k < Nk) q -= b[(size_t)v * Nk + k];
+            q = fmaxf(q, 0.f);
+            if (k >= Nk || (dead && dead[k])) q = 0.f;
+            p[i] = q;
+        }
+        TO *dst = P + (size_t)j * ldP + k0;
+        if (k0 + 8 <= ldP) store8<TO>(dst, p);
+        else
+            for (int i = 0; i < 8 && k0 + i < ldP; ++i) store1<TO>(dst + i, p[i]);
+    }
+}
+
+}  // namespace fhr
+
+using namespace fhr;
+
+extern "C" fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *p, const uint16_t *y, const uint16_t *y0,
+                                    const uint8_t *bg, const uint8_t *dead, float *b_out, void *P) {
+    if (!ctx) return FHR_ERR_ARG;
+    FHR_ARG(p, "params is null");
+    FHR_ARG(p->Nv > 0 && p->Nr > 0 && p->Nc > 0 && p->Nk > 0, "sizes must be positive");
+    FHR_ARG(p->ldP >= p->Nk, "ldP < Nk");
+    FHR_ARG(p->p_dtype == FHR_F32 || p->p_dtype == FHR_BF16, "bad p_dtype");
+    FHR_ARG(p->ldP % (p->p_dtype == FHR_BF16 ? 8 : 4) == 0, "ldP must make rows 16-byte aligned");
+    FHR_ARG(y && y0 && P, "null pointer argument");
+    FHR_ARG(!bg || b_out, "b_out is required with a background mask");
+    FHR_ARG(aligned(P, 16), "P must be 16-byte aligned");
+    FHR_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const float *b = nullptr;
+    if (bg) {
+        dim3 grid((unsigned)cdiv(p->Nk, 128), (unsigned)p->Nv);
+        offset_reduce_kernel<<<grid, 128, 0, st>>>(y, y0, bg, p->Nv, p->Nr, p->Nc, p->Nk, b_out);
+        FHR_LAUNCHED();
+        b = b_out;
+    }
+    // the 8-bin chunks of the f32 output need ldP % 8 == 0 for full 32-byte stores;
+    // other ldP take the scalar store tail
+    const bool vec = (p->Nk % 8 == 0) && aligned(y, 16) && aligned(y0, 16);
+    const int64_t total = (int64_t)p->Nv * p->Nc * p->Nr * (p->ldP / 8 + (p->ldP % 8 ? 1 : 0));
+    const int blocks = (int)std::min<int64_t>(cdiv(total, 256), (int64_t)ctx->sm_count * 16);
+    const int ldp8 = p->ldP;
+#define LAUNCH(V, T)                                                                                     \
+    FHR_TIMED(TM_NORMALISE, (normalise_kernel<V, T><<<blocks, 256, 0, st>>>(y, y0, dead, b, p->Nv, p->Nr, p->Nc, \
+                                                                            p->Nk, ldp8, reinterpret_cast<T *>(P))))
+    if (p->p_dtype == FHR_F32) {
+        if (vec) LAUNCH(true, float);
+        else LAUNCH(false, float);
+    } else {
+        if (vec) LAUNCH(true, __nv_bfloat16);
+        else LAUNCH(false, __nv_bfloat16);
+    }
+#undef LAUNCH
+    return FHR_OK;
+}

@@ -1,0 +1,188 @@
+// Projector tables, launches and the standalone projector entry points.
+#include "proj.cuh"
+
+namespace fhr {
+
+__device__ __forceinline__ double footprint_cdf(double s, double hi, double lo) {
+    const double t2 = 0.5 * (hi + lo), t1 = 0.5 * (hi - lo);
+    if (s <= -t2) return 0.0;
+    if (s >= t2) return 1.0;
+    if (s <= -t1) return (s + t2) * (s + t2) / (2.0 * hi * lo);
+    if (s <= t1) return lo / (2.0 * hi) + (s + t1) / hi;
+    return 1.0 - (t2 - s) * (t2 - s) / (2.0 * hi * lo);
+}
+
+// area of pixel (px, py) inside the unit strip centred at uc, direction (c, s)
+// not inlined: both tables call the one compiled instance, so equal inputs give equal bits
+__device__ __noinline__ double strip_area(double c, double s, double px, double py, double uc) {
+    const double a = fabs(c), b = fabs(s);
+    const double hi = fmax(a, b), lo = fmin(a, b);
+    const double u0 = px * c + py * s;
+    return footprint_cdf(uc + 0.5 - u0, hi, lo) - footprint_cdf(uc - 0.5 - u0, hi, lo);
+}
+
+__device__ __forceinline__ void view_dir(const double *angles, int v, int Nv, double *c, double *s) {
+    const double th = angles ? angles[v] : (double)v * (3.141592653589793 / (double)Nv);
+    sincos(th, s, c);
+}
+
+// forward table: one thread per (v, c, line)
+__global__ void proj_table_fw(const double *angles, int N, int Nc, int Nv, ProjTables t) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)Nv * Nc * N) return;
+    const int l = (int)(idx % N);
+    const int c = (int)((idx / N) % Nc);
+    const int v = (int)(idx / ((int64_t)N * Nc));
+    double cs, sn;
+    view_dir(angles, v, Nv, &cs, &sn);
+    const double h = 0.5 * (N - 1);
+    const double uc = c - 0.5 * (Nc - 1);
+    const double half = 0.5 + 0.5 * (fabs(cs) + fabs(sn));
+    const bool rows = fabs(cs) >= fabs(sn);
+    double center, R;
+    if (rows) {
+        const double py = l - h;
+        center = (uc - py * sn) / cs + h;
+        R = half / fabs(cs);
+    } else {
+        const double px = l - h;
+        center = (uc - px * cs) / sn + h;
+        R = half / fabs(sn);
+    }
+    int s0 = (int)floor(center - R) + 1;
+    s0 = max(0, min(s0, N - 4));
+    float w[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int q = s0 + m;
+        const double px = rows ? q - h : l - h;
+        const double py = rows ? l - h : q - h;
+        w[m] = (float)strip_area(cs, sn, px, py, uc);
+    }
+    t.fw[idx] = make_float4(w[0], w[1], w[2], w[3]);
+    t.fws[idx] = s0;
+    if (c == 0 && l == 0) t.rowmaj[v] = rows ? 1 : 0;
+}
+
+// backward table: one thread per (v, pixel)
+__global__ void proj_table_bk(const double *angles, int N, int Nc, int Nv, ProjTables t) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)Nv * N * N) return;
+    const int pix = (int)(idx % ((int64_t)N * N));
+    const int v = (int)(idx / ((int64_t)N * N));
+    const int iy = pix / N, ix = pix % N;
+    double cs, sn;
+    view_dir(angles, v, Nv, &cs, &sn);
+    const double h = 0.5 * (N - 1);
+    const double px = ix - h, py = iy - h;
+    const double u0 = px * cs + py * sn;
+    const double half = 0.5 + 0.5 * (fabs(cs) + fabs(sn));
+    int c0 = (int)floor(u0 + 0.5 * (Nc - 1) - half) + 1;
+    c0 = max(0, min(c0, Nc - 3));
+    float w[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) w[m] = (float)strip_area(cs, sn, px, py, (c0 + m) - 0.5 * (Nc - 1));
+    t.bk[idx] = make_float4(w[0], w[1], w[2], (float)c0);
+}
+
+void proj_tables_carve(Carve &c, int N, int Nc, int Nv, ProjTables *t) {
+    ProjTables tt;
+    tt.fw = c.take<float4>((size_t)Nv * Nc * N);
+    tt.fws = c.take<int>((size_t)Nv * Nc * N);
+    tt.rowmaj = c.take<uint8_t>((size_t)Nv);
+    tt.bk = c.take<float4>((size_t)Nv * N * N);
+    if (t) *t = tt;
+}
+
+fhr_status check_geom(fhr_ctx *ctx, const fhr_geom *g, int Wl) {
+    FHR_ARG(g, "geometry is null");
+    FHR_ARG(g->N >= 4, "N must be >= 4");
+    FHR_ARG(g->Nc >= 3, "Nc must be >= 3");
+    FHR_ARG(g->Nv >= 1 && g->Nr >= 1, "Nv and Nr must be positive");
+    FHR_ARG((int64_t)g->N * g->N < (1ll << 31) && (int64_t)g->Nv * g->Nc < (1ll << 31), "geometry too large");
+    FHR_ARG(Wl >= 1 && Wl <= 4096 && (Wl % 4 == 0 || Wl <= 1024), "Wl must be 1..1024, or a multiple of 4 up to 4096");
+    return FHR_OK;
+}
+
+fhr_status proj_build_tables(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t) {
+    const int64_t nf = (int64_t)g->Nv * g->Nc * g->N, nb = (int64_t)g->Nv * g->N * g->N;
+    proj_table_fw<<<(unsigned)cdiv(nf, 256), 256, 0, ctx->stream>>>(g->angles, g->N, g->Nc, g->Nv, t);
+    FHR_LAUNCHED();
+    proj_table_bk<<<(unsigned)cdiv(nb, 256), 256, 0, ctx->stream>>>(g->angles, g->N, g->Nc, g->Nv, t);
+    FHR_LAUNCHED();
+    return FHR_OK;
+}
+
+fhr_status proj_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *x, float *y,
+                        const float *V) {
+    const GatherShape s = gather_shape(Wl);
+    const int items = g->Nv * g->Nc;
+    const unsigned blocks = (unsigned)cdiv(items, s.ipb);
+    if (s.vw == 4)
+        FHR_TIMED(TM_PROJ_FWD, (proj_fwd_kernel<4><<<blocks, s.threads, 0, ctx->stream>>>(x, y, V, t, g->N, g->Nc,
+                                                                                          g->Nv, Wl)));
+    else
+        FHR_TIMED(TM_PROJ_FWD, (proj_fwd_kernel<1><<<blocks, s.threads, 0, ctx->stream>>>(x, y, V, t, g->N, g->Nc,
+                                                                                          g->Nv, Wl)));
+    return FHR_OK;
+}
+
+fhr_status proj_backward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *y, float *x) {
+    const GatherShape s = gather_shape(Wl);
+    const int items = g->N * g->N;
+    const unsigned blocks = (unsigned)cdiv(items, s.ipb);
+    if (s.vw == 4)
+        FHR_TIMED(TM_PROJ_BWD, (proj_bwd_kernel<4><<<blocks, s.threads, 0, ctx->stream>>>(y, x, t, g->N, g->Nc,
+                                                                                          g->Nv, Wl)));
+    else
+        FHR_TIMED(TM_PROJ_BWD, (proj_bwd_kernel<1><<<blocks, s.threads, 0, ctx->stream>>>(y, x, t, g->N, g->Nc,
+                                                                                          g->Nv, Wl)));
+    return FHR_OK;
+}
+
+static size_t proj_ws(const fhr_geom *g, ProjTables *t, void *base) {
+    Carve c(base);
+    c.take<int>(kStatusBytes / sizeof(int));
+    proj_tables_carve(c, g->N, g->Nc, g->Nv, t);
+    return c.size();
+}
+
+}  // namespace fhr
+
+using namespace fhr;
+
+extern "C" fhr_status fhr_projector_workspace_size(fhr_ctx *ctx, const fhr_geom *g, size_t *bytes) {
+    if (!ctx) return FHR_ERR_ARG;
+    FHR_TRY(check_geom(ctx, g, 1));
+    FHR_ARG(bytes, "bytes is null");
+    *bytes = proj_ws(g, nullptr, nullptr);
+    return FHR_OK;
+}
+
+static fhr_status proj_common(fhr_ctx *ctx, const fhr_geom *g, int Wl, const void *in, void *out, void *ws,
+                              size_t ws_bytes, ProjTables *t) {
+    FHR_TRY(check_geom(ctx, g, Wl));
+    FHR_ARG(in && out && ws, "null pointer argument");
+    FHR_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
+    FHR_ARG(Wl % 4 != 0 || (aligned(in, 16) && aligned(out, 16)), "x and y must be 16-byte aligned when Wl % 4 == 0");
+    const size_t need = proj_ws(g, t, ws);
+    FHR_ARG(ws_bytes >= need, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+    FHR_CUDA(cudaSetDevice(ctx->device));
+    return proj_build_tables(ctx, g, *t);
+}
+
+extern "C" fhr_status fhr_project(fhr_ctx *ctx, const fhr_geom *g, int Wl, const float *x, float *y, void *ws,
+                                  size_t ws_bytes) {
+    if (!ctx) return FHR_ERR_ARG;
+    ProjTables t;
+    FHR_TRY(proj_common(ctx, g, Wl, x, y, ws, ws_bytes, &t));
+    return proj_forward(ctx, g, t, Wl, x, y, nullptr);
+}
+
+extern "C" fhr_status fhr_backproject(fhr_ctx *ctx, const fhr_geom *g, int Wl, const float *y, float *x, void *ws,
+                                      size_t ws_bytes) {
+    if (!ctx) return FHR_ERR_ARG;
+    ProjTables t;
+    FHR_TRY(proj_common(ctx, g, Wl, y, x, ws, ws_bytes, &t));
+    return proj_backward(ctx, g, t, Wl, y, x);
+}

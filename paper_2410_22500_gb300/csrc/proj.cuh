@@ -1,0 +1,146 @@
+// Parallel-beam strip-area projector (A of Eq. porj_matd_rel / Eq. recon).
+//
+// A_{(v,c),i} = area(unit pixel i intersect the unit-width strip of bin c at
+// view v).  It is the integral over the bin of the pixel's trapezoidal
+// footprint, so it has a closed form (footprint_cdf below).  The weights are
+// evaluated once per call in double precision into two tables:
+//   forward  [Nv][Nc][N] lines: along the image axis most parallel to the
+//            rays, 4 candidate pixels per line (a strip crosses at most 4),
+//   backward [Nv][N*N]: 3 candidate bins per pixel (a footprint spans <= 3),
+// both rounded to float from the same double, so A^T is the exact transpose
+// of A.  The two gathers apply each weight to a vector of Wl values per
+// pixel / ray (all slices and subspace channels at once), so every access is
+// a contiguous, vectorised read of Wl floats.
+#pragma once
+
+#include "common.cuh"
+
+namespace fhr {
+
+struct ProjTables {
+    float4 *fw;        // [Nv][Nc][N] weights of candidates s0..s0+3
+    int *fws;          // [Nv][Nc][N] s0
+    uint8_t *rowmaj;   // [Nv] 1: lines are image rows (|cos| >= |sin|)
+    float4 *bk;        // [Nv][N*N] {w0, w1, w2, c0}
+};
+
+template <int VW>
+struct VecF;
+template <>
+struct VecF<4> {
+    using T = float4;
+    __device__ __forceinline__ static float4 ld(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+    __device__ __forceinline__ static void st(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+    __device__ __forceinline__ static void fma(float4 &a, float w, float4 x) {
+        a.x = fmaf(w, x.x, a.x); a.y = fmaf(w, x.y, a.y); a.z = fmaf(w, x.z, a.z); a.w = fmaf(w, x.w, a.w);
+    }
+    __device__ __forceinline__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ __forceinline__ static float get(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+    __device__ __forceinline__ static void set(float4 &v, int e, float f) {
+        if (e == 0) v.x = f; else if (e == 1) v.y = f; else if (e == 2) v.z = f; else v.w = f;
+    }
+};
+template <>
+struct VecF<1> {
+    using T = float;
+    __device__ __forceinline__ static float ld(const float *p) { return *p; }
+    __device__ __forceinline__ static void st(float *p, float v) { *p = v; }
+    __device__ __forceinline__ static void fma(float &a, float w, float x) { a = fmaf(w, x, a); }
+    __device__ __forceinline__ static float zero() { return 0.f; }
+    __device__ __forceinline__ static float get(const float &v, int) { return v; }
+    __device__ __forceinline__ static void set(float &v, int, float f) { v = f; }
+};
+
+// y[v][c][w] = sum over lines and candidates of A * x[pixel][w].
+// Thread = (item (v, c), chunk of VW values).  With V non-null the output is
+// the residual V - A x.
+template <int VW>
+__global__ void __launch_bounds__(1024) proj_fwd_kernel(const float *__restrict__ x, float *__restrict__ y,
+                                                        const float *__restrict__ V, ProjTables t, int N, int Nc,
+                                                        int Nv, int Wl) {
+    using VF = VecF<VW>;
+    const int CH = Wl / VW;
+    const int ipb = blockDim.x / CH;
+    const int item = blockIdx.x * ipb + threadIdx.x / CH;
+    const int ch = threadIdx.x % CH;
+    if (threadIdx.x >= ipb * CH || item >= Nv * Nc) return;
+    const int v = item / Nc;
+    const bool rows = t.rowmaj[v] != 0;
+    const float4 *fw = t.fw + (size_t)item * N;
+    const int *fs = t.fws + (size_t)item * N;
+    const int lstride = rows ? N : 1;     // pixel index = l * lstride + q * qstride
+    const int qstride = rows ? 1 : N;
+    typename VF::T acc = VF::zero();
+    const float *xc = x + ch * VW;
+    for (int l = 0; l < N; ++l) {
+        const float4 w = __ldg(fw + l);
+        const int s0 = __ldg(fs + l);
+        const int p0 = l * lstride + s0 * qstride;
+        if (w.x != 0.f) VF::fma(acc, w.x, VF::ld(xc + (size_t)p0 * Wl));
+        if (w.y != 0.f) VF::fma(acc, w.y, VF::ld(xc + (size_t)(p0 + qstride) * Wl));
+        if (w.z != 0.f) VF::fma(acc, w.z, VF::ld(xc + (size_t)(p0 + 2 * qstride) * Wl));
+        if (w.w != 0.f) VF::fma(acc, w.w, VF::ld(xc + (size_t)(p0 + 3 * qstride) * Wl));
+    }
+    float *yo = y + (size_t)item * Wl + ch * VW;
+    if (V) {
+        typename VF::T vv = VF::ld(V + (size_t)item * Wl + ch * VW);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) VF::set(acc, e, VF::get(vv, e) - VF::get(acc, e));
+    }
+    VF::st(yo, acc);
+}
+
+// x[pixel][w] = sum over views and candidate bins of A * y[v][c][w].
+template <int VW>
+__device__ __forceinline__ typename VecF<VW>::T backproject_at(const float *__restrict__ y, const ProjTables &t, int N,
+                                                               int Nc, int Nv, int Wl, int pix, int ch) {
+    using VF = VecF<VW>;
+    typename VF::T acc = VF::zero();
+    const float *yc = y + ch * VW;
+    const size_t NN = (size_t)N * N;
+    for (int v = 0; v < Nv; ++v) {
+        const float4 w = __ldg(t.bk + v * NN + pix);
+        const size_t row = (size_t)v * Nc + (int)w.w;
+        if (w.x != 0.f) VF::fma(acc, w.x, VF::ld(yc + row * Wl));
+        if (w.y != 0.f) VF::fma(acc, w.y, VF::ld(yc + (row + 1) * Wl));
+        if (w.z != 0.f) VF::fma(acc, w.z, VF::ld(yc + (row + 2) * Wl));
+    }
+    return acc;
+}
+
+template <int VW>
+__global__ void __launch_bounds__(1024) proj_bwd_kernel(const float *__restrict__ y, float *__restrict__ x,
+                                                        ProjTables t, int N, int Nc, int Nv, int Wl) {
+    using VF = VecF<VW>;
+    const int CH = Wl / VW;
+    const int ipb = blockDim.x / CH;
+    const int pix = blockIdx.x * ipb + threadIdx.x / CH;
+    const int ch = threadIdx.x % CH;
+    if (threadIdx.x >= ipb * CH || pix >= N * N) return;
+    VF::st(x + (size_t)pix * Wl + ch * VW, backproject_at<VW>(y, t, N, Nc, Nv, Wl, pix, ch));
+}
+
+// Launch shape for the gathers: CH = Wl / VW threads per item, items per block
+// so that a block holds about `target` threads.
+struct GatherShape {
+    int vw, ch, ipb, threads;
+};
+
+static inline GatherShape gather_shape(int Wl, int target = 256) {
+    GatherShape g;
+    g.vw = (Wl % 4 == 0) ? 4 : 1;
+    g.ch = Wl / g.vw;
+    g.ipb = std::max(1, target / g.ch);
+    g.threads = g.ipb * g.ch;
+    return g;
+}
+
+size_t proj_tables_bytes(int N, int Nc, int Nv);
+void proj_tables_carve(Carve &c, int N, int Nc, int Nv, ProjTables *t);
+fhr_status proj_build_tables(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t);
+fhr_status proj_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *x, float *y,
+                        const float *V);
+fhr_status proj_backward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *y, float *x);
+fhr_status check_geom(fhr_ctx *ctx, const fhr_geom *g, int Wl);
+
+}  // namespace fhr

@@ -285,7 +285,10 @@ def counts_numpy(pb: Problem, noise: bool = True):
 
 
 def counts_torch(pb: Problem, device="cuda", chunk_views: int = 8):
-    """Counts (y, y0) as uint16 torch tensors drawn on `device` (large cases).
+    """Counts (y, y0) drawn on `device` (large cases), as int16 tensors holding
+    the uint16 bit patterns (torch's uint16 support is partial; the library
+    reads the bytes as uint16, and `.cpu().numpy().view(np.uint16)` recovers
+    the counts on the host).
 
     Same distribution as counts_numpy; torch's seeded generator draws the
     Poisson samples view by view so peak memory stays bounded."""
@@ -297,18 +300,18 @@ def counts_torch(pb: Problem, device="cuda", chunk_views: int = 8):
     C = torch.from_numpy(chords(pb.phantom, g).reshape(g.Nv, g.Nr * g.Nc, -1)).to(device, torch.float32)
     mu = torch.from_numpy(pb.spectra.T.copy()).to(device, torch.float32)   # [Nm][Nk]
     dead = torch.from_numpy(pb.dead_bins.astype(bool)).to(device)
-    y = torch.empty((g.Nv, g.Nr, g.Nc, pb.Nk), dtype=torch.uint16, device=device)
+    y = torch.empty((g.Nv, g.Nr, g.Nc, pb.Nk), dtype=torch.int16, device=device)
     yv = y.view(g.Nv, g.Nr * g.Nc, pb.Nk)
     for v0 in range(0, g.Nv, chunk_views):
         v1 = min(g.Nv, v0 + chunk_views)
         lam = pb.I0 * torch.exp(-(C[v0:v1] @ mu))
         s = torch.poisson(lam, generator=gen).clamp_(max=65535)
         s[..., dead] = 0
-        yv[v0:v1] = s.to(torch.int32).to(torch.uint16)
+        yv[v0:v1] = s.to(torch.int32).to(torch.int16)
         del lam, s
     y0f = torch.poisson(torch.full((g.Nr, g.Nc, pb.Nk), pb.I0, device=device), generator=gen).clamp_(max=65535)
     y0f[..., dead] = 0
-    y0 = y0f.to(torch.int32).to(torch.uint16)
+    y0 = y0f.to(torch.int32).to(torch.int16)
     return y, y0
 
 

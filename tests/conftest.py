@@ -19,3 +19,23 @@ def orc():
 
     oracle.lib()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def lib_path():
+    from paper_2410_22500_gb300 import build
+
+    return build.build()
+
+
+@pytest.fixture(scope="session")
+def fx(lib_path):
+    """A libfhr context on cuda:0 (GPU tests only; fails loudly without a GPU)."""
+    import torch
+    from paper_2410_22500_gb300 import fhr
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    ctx = fhr.Context(0)
+    yield ctx
+    torch.cuda.synchronize()
+    ctx.close()

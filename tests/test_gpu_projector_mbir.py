@@ -1,0 +1,127 @@
+"""GPU parity of the strip-area projector pair and of the MBIR (SQS, qGGMRF) reconstruction, Eq. (recon)."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _angles(Nv):
+    return np.arange(Nv) * (math.pi / Nv)
+
+
+GEOMS = [(32, 48, 60, 3), (16, 23, 17, 8), (9, 13, 7, 1), (24, 40, 45, 12), (8, 12, 4, 5)]
+
+
+@pytest.mark.parametrize("N,Nc,Nv,Wl", GEOMS)
+def test_forward_matches_oracle(fx, orc, N, Nc, Nv, Wl):
+    rng = np.random.default_rng(200 + N)
+    x = rng.uniform(0, 1, size=(N, N, Wl)).astype(np.float32)
+    y = fx.project(_dev(x), Nc, Nv).cpu().numpy()
+    ref = orc.project(x.astype(np.float64), Nc, _angles(Nv))
+    assert _rel(y, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("N,Nc,Nv,Wl", GEOMS)
+def test_backward_matches_oracle(fx, orc, N, Nc, Nv, Wl):
+    rng = np.random.default_rng(300 + N)
+    e = rng.normal(size=(Nv, Nc, Wl)).astype(np.float32)
+    x = fx.backproject(_dev(e), N).cpu().numpy()
+    ref = orc.backproject(e.astype(np.float64), N, _angles(Nv))
+    assert _rel(x, ref) <= 1e-5
+
+
+def test_adjointness_fp32(fx):
+    rng = np.random.default_rng(400)
+    N, Nc, Nv, Wl = 40, 60, 50, 8
+    x = rng.normal(size=(N, N, Wl)).astype(np.float32)
+    y = rng.normal(size=(Nv, Nc, Wl)).astype(np.float32)
+    Ax = fx.project(_dev(x), Nc, Nv).cpu().numpy().astype(np.float64)
+    Aty = fx.backproject(_dev(y), N).cpu().numpy().astype(np.float64)
+    lhs = np.sum(Ax * y)
+    rhs = np.sum(x * Aty)
+    scale = np.sqrt(np.sum(Ax * Ax) * np.sum(y * y))
+    assert abs(lhs - rhs) <= 1e-6 * scale
+
+
+def test_exact_transpose_on_unit_vectors(fx, orc):
+    # the two tables hold bit-identical weights: A e_i (forward) equals row i of A^T
+    # applied to unit sinogram vectors, compared through the dense oracle matrix
+    N, Nc, Nv = 6, 10, 7
+    th = _angles(Nv)
+    A = orc.system_matrix(N, Nc, th)
+    X = np.zeros((N, N, N * N), np.float32)
+    for i in range(N * N):
+        X[i // N, i % N, i] = 1
+    Af = fx.project(_dev(X), Nc, Nv).cpu().numpy().reshape(Nv * Nc, N * N)
+    Y = np.eye(Nv * Nc, dtype=np.float32).reshape(Nv, Nc, Nv * Nc)
+    Ab = fx.backproject(_dev(Y), N).cpu().numpy().reshape(N * N, Nv * Nc)
+    np.testing.assert_array_equal(Af, Ab.T)
+    np.testing.assert_allclose(Af, A, atol=6e-8)
+
+
+def test_custom_angles(fx, orc):
+    import torch
+
+    rng = np.random.default_rng(401)
+    N, Nc, Nv, Wl = 16, 24, 11, 4
+    th = np.sort(rng.uniform(0, math.pi, Nv))
+    x = rng.uniform(size=(N, N, Wl)).astype(np.float32)
+    y = fx.project(_dev(x), Nc, Nv, angles=torch.from_numpy(th).cuda()).cpu().numpy()
+    assert _rel(y, orc.project(x.astype(np.float64), Nc, th)) <= 1e-5
+
+
+def _sino(orc, N, Nc, Nv, Nr, K, seed, noise=0.02):
+    rng = np.random.default_rng(seed)
+    xt = np.zeros((N, N, Nr * K))
+    c = N // 2
+    xt[c - N // 4:c + N // 4, c - N // 5:c + N // 3] = rng.uniform(0.5, 1.0, size=Nr * K)
+    V = orc.project(xt, Nc, _angles(Nv))
+    return (V + noise * rng.normal(size=V.shape) * V.max()).astype(np.float32)
+
+
+@pytest.mark.parametrize("N,Nc,Nv,Nr,K,momentum,p", [(20, 30, 24, 2, 3, False, 1.2), (16, 24, 18, 3, 2, True, 1.2),
+                                                     (24, 36, 30, 1, 3, False, 1.5), (12, 18, 10, 4, 1, True, 2.0)])
+def test_mbir_matches_oracle(fx, orc, N, Nc, Nv, Nr, K, momentum, p):
+    V = _sino(orc, N, Nc, Nv, Nr, K, seed=N + Nr)
+    sv, sx = orc.mbir_sigmas(V.astype(np.float64).reshape(-1, K), K, Nc)
+    iters = 20
+    ref = orc.mbir(V.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, p=p, iters=iters, momentum=momentum)
+    got = fx.reconstruct(_dev(V), N, Nr, K, iters, p=p, momentum=momentum).cpu().numpy()
+    assert _rel(got, ref) <= 1e-4
+    # explicit sigmas take the same path
+    got2 = fx.reconstruct(_dev(V), N, Nr, K, iters, p=p, momentum=momentum, sigma_v=sv, sigma_x=sx).cpu().numpy()
+    assert _rel(got2, ref) <= 1e-4
+
+
+def test_mbir_no_prior_and_warm_start(fx, orc):
+    N, Nc, Nv, Nr, K = 12, 18, 16, 1, 2
+    V = _sino(orc, N, Nc, Nv, Nr, K, seed=5)
+    sv, sx = np.array([0.5, 1.0]), np.array([1.0, 1.0])
+    rng = np.random.default_rng(6)
+    x0 = rng.uniform(0, 0.5, size=(N, N, Nr * K)).astype(np.float32)
+    ref = orc.mbir(V.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, beta=0.0, iters=15,
+                   x0=x0.astype(np.float64))
+    got = fx.reconstruct(_dev(V), N, Nr, K, 15, beta=0.0, sigma_v=sv, sigma_x=sx, xs=_dev(x0)).cpu().numpy()
+    assert _rel(got, ref) <= 1e-4
+
+
+def test_mbir_zero_channel(fx, orc):
+    # an all-zero subspace channel reconstructs to zero (sigma defaults to 1 there)
+    N, Nc, Nv, Nr, K = 10, 16, 12, 1, 2
+    V = _sino(orc, N, Nc, Nv, Nr, K, seed=7)
+    V[..., 1] = 0
+    got = fx.reconstruct(_dev(V), N, Nr, K, 10).cpu().numpy()
+    assert np.all(got[..., 1] == 0)
+    assert np.all(got >= 0)
