@@ -142,6 +142,29 @@ fhr_status fhr_decompose_workspace_size(fhr_ctx *ctx, const fhr_nmf_params *prm,
 fhr_status fhr_decompose(fhr_ctx *ctx, const fhr_nmf_params *prm, const void *P,
                          float *D, float *W, double *obj, void *ws, size_t ws_bytes);
 
+/* The same decomposition without a workspace argument, for callers that
+ * cannot allocate device memory or cannot pass a workspace.  Examples: a
+ * plugin bound to a fixed C signature, a framework that owns all device
+ * memory through its own allocator, or a latency-critical loop where a
+ * cudaMalloc (which can synchronise the device) is not allowed.  The paper has no
+ * counterpart; this is a deployment form of fhr_decompose and runs its kernels.
+ *   - Scratch is one static device array of 32 MiB inside the library.  Every
+ *     GPU that loads the library holds it until the process exits.  Problems
+ *     that need more (fhr_decompose_workspace_size) fail with FHR_ERR_ARG and
+ *     a message; nothing is launched.
+ *   - The call allocates nothing: no cudaMalloc, cudaFree or allocating
+ *     library routine.  Event timers (fhr_profile_enable) are suspended for it.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   - All calls share the one array (it keeps the last call's contents; the
+ *     call clears what must start at zero).  Calls that overlap on the GPU,
+ *     from any stream or thread, race on it: serialise them.
+ *   - Device-side status words are kept in the array and are not returned;
+ *     a non-finite objective still shows up in obj.
+ * Arguments as for fhr_decompose. */
+fhr_status fhr_decompose_static(fhr_ctx *ctx, const fhr_nmf_params *prm, const void *P,
+                                float *D, float *W, double *obj);
+
 /* ------------------------------------------------------------------------
  * Parallel-beam projector of Eq. (porj_matd_rel)/(recon): the strip-area
  * model A_{(v,c),i} = area(pixel i intersect strip of bin c at view v).

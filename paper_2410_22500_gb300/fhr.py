@@ -23,6 +23,7 @@ ENTRY_POINTS = (
     "fhr_normalise", "fhr_decompose_workspace_size", "fhr_decompose", "fhr_projector_workspace_size",
     "fhr_project", "fhr_backproject", "fhr_reconstruct_workspace_size", "fhr_reconstruct", "fhr_expand",
     "fhr_pipeline_workspace_size", "fhr_pipeline", "fhr_profile_enable", "fhr_profile_read",
+    "fhr_decompose_static",
 )
 
 
@@ -90,6 +91,7 @@ def load():
                                  ctypes.c_int, vp, vp, ctypes.c_int, vp]
         L.fhr_pipeline_workspace_size.argtypes = [vp, ctypes.POINTER(PipelineParams), szp]
         L.fhr_pipeline.argtypes = [vp, ctypes.POINTER(PipelineParams), vp, vp, vp, vp, vp, vp, vp, vp, sz]
+        L.fhr_decompose_static.argtypes = [vp, ctypes.POINTER(NmfParams), vp, vp, vp, vp]
         L.fhr_profile_enable.argtypes = [vp, ctypes.c_int]
         L.fhr_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_double)]
