@@ -79,13 +79,13 @@ __global__ void nmf_init_given(const float *D0, int Nk, int K, double *D64, NmfS
 // Q64[k][s] = sum over CTAs of Qpart (FP64, fixed order).  The last block also
 // reduces the K x K Gram partials and ||P||^2.
 __global__ void nmf_reduce(const float *Qpart, const float *Gpart, const float *ssqpart, int grid, int nval,
-                           int K, double *Q64, double *GW64, double *ssq64) {
+                           int K, double *Q64, double *GW64, double *ssq64, int want_ssq) {
     __shared__ double part[8][33];
     const int tid = threadIdx.x;
     const int lane = tid & 31, ch = tid >> 5;   // 8 chunks over the CTA partials
     if (blockIdx.x == gridDim.x - 1) {
         // Gram and ||P||^2: nsmall = K*K + 1 values
-        const int nsmall = K * K + 1;
+        const int nsmall = K * K + (want_ssq ? 1 : 0);
         for (int v0 = 0; v0 < nsmall; v0 += 32) {
             const int v = v0 + lane;
             double acc = 0.0;
@@ -295,14 +295,16 @@ extern "C" fhr_status fhr_decompose(fhr_ctx *ctx, const fhr_nmf_params *p, const
     a.ssqpart = w.ssqpart;
     a.status = w.status;
     a.mode = PASS_HALS;
+    a.want_ssq = 1;
     const int nval = Nk * K;
     const int nred = (int)cdiv(nval, 32) + 1;
     const int nupd = (int)cdiv(Nk, kUpdThreads);
     for (int t = 0; t < p->iters; ++t) {
         a.st = &w.state[t & 1];
+        a.want_ssq = t == 0;   // ||P||^2 once; later iterations reuse it
         FHR_TRY(launch_pass(ctx, cfg, a));
         FHR_TIMED(TM_NMF_REDUCE, (nmf_reduce<<<nred, 256, 0, st>>>(w.Qpart, w.Gpart, w.ssqpart, cfg.grid, nval, K,
-                                                                   w.Q64, w.GW64, w.ssq64)));
+                                                                   w.Q64, w.GW64, w.ssq64, a.want_ssq)));
         FHR_TIMED(TM_NMF_UPDATE,
                   (nmf_update_d<<<nupd, kUpdThreads, 0, st>>>(w.Q64, w.GW64, w.ssq64, w.D64, Nk, K, &w.state[t & 1],
                                                               &w.state[(t + 1) & 1], w.Bpart, w.counter,

@@ -16,33 +16,31 @@ static PassFn<TP> pick(int K, int cpt);
 template <>
 PassFn<float> pick<float>(int K, int cpt) {
     using TP = float;
-    CASE(1, 1) CASE(1, 2) CASE(1, 3) CASE(2, 1) CASE(2, 2) CASE(2, 3) CASE(3, 1) CASE(3, 2) CASE(3, 3)
-    CASE(4, 1) CASE(4, 2) CASE(4, 3) CASE(5, 1) CASE(5, 2) CASE(5, 3) CASE(6, 1) CASE(6, 2) CASE(7, 1)
-    CASE(7, 2) CASE(8, 1) CASE(8, 2)
+    CASE(1, 1) CASE(1, 2) CASE(1, 3) CASE(1, 4) CASE(2, 1) CASE(2, 2) CASE(2, 3) CASE(2, 4)
+    CASE(3, 1) CASE(3, 2) CASE(3, 3) CASE(3, 4) CASE(4, 1) CASE(4, 2) CASE(4, 3) CASE(4, 4)
+    CASE(5, 1) CASE(5, 2) CASE(5, 3) CASE(6, 1) CASE(6, 2) CASE(6, 3) CASE(7, 1) CASE(7, 2) CASE(7, 3)
+    CASE(8, 1) CASE(8, 2) CASE(8, 3)
     return nullptr;
 }
 
 template <>
 PassFn<__nv_bfloat16> pick<__nv_bfloat16>(int K, int cpt) {
     using TP = __nv_bfloat16;
-    CASE(1, 1) CASE(2, 1) CASE(3, 1) CASE(4, 1) CASE(5, 1) CASE(6, 1) CASE(7, 1) CASE(8, 1)
+    CASE(1, 1) CASE(1, 2) CASE(2, 1) CASE(2, 2) CASE(3, 1) CASE(3, 2) CASE(4, 1) CASE(4, 2) CASE(5, 1) CASE(5, 2)
+    CASE(6, 1) CASE(7, 1) CASE(8, 1)
     return nullptr;
 }
 #undef CASE
 
+// Columns per thread: Q for the owned columns stays in registers for the whole
+// launch (cpt * vec * K floats); D is read from shared memory.
 static int max_cpt(int K, int vec) {
-    // D and Q for the owned columns stay in registers: 2 * cpt * vec * K <= 128
-    int c = 128 / (2 * vec * K);
-    if (vec == 8) c = 1;
-    return c < 1 ? 1 : (c > 3 ? 3 : c);
+    if (vec == 8) return K <= 5 ? 2 : 1;
+    return K <= 4 ? 4 : 3;
 }
 
 static size_t pass_smem(int K, int NT, int ldP, int esize, int stages) {
-    const int ROWS = kPassRows, NW = NT / 32;
-    size_t b = (size_t)stages * ROWS * ldP * esize;
-    b += sizeof(float) * ((size_t)NW * ROWS * K + ROWS * K + K * K + 2 * K + ROWS * K * K);
-    b = (b + 7) / 8 * 8 + 2 * stages * sizeof(uint64_t);
-    return b;
+    return pass_smem_layout(K, NT / 32, ldP, esize, stages).total;
 }
 
 fhr_status pass_config(fhr_ctx *ctx, int K, int Nk, int ldP, int p_dtype, PassConfig *cfg) {
@@ -50,17 +48,17 @@ fhr_status pass_config(fhr_ctx *ctx, int K, int Nk, int ldP, int p_dtype, PassCo
     const int esize = p_dtype == FHR_BF16 ? 2 : 4;
     const int ncol = ldP / vec;
     // columns per thread: the largest count whose column balance is within 2% of the best
-    int nts[4] = {0, 0, 0, 0};
-    double effs[4] = {-1, -1, -1, -1}, best = -1;
+    int nts[5] = {0, 0, 0, 0, 0};
+    double effs[5] = {-1, -1, -1, -1, -1}, best = -1;
     for (int cpt = 1; cpt <= max_cpt(K, vec); ++cpt) {
         int nt = (int)((cdiv(ncol, cpt) + 31) / 32 * 32);
-        if (nt + 32 > 256) continue;
+        if (nt + 64 > 256) continue;
         nts[cpt] = nt;
         effs[cpt] = (double)ncol / ((double)nt * cpt);
         if (effs[cpt] > best) best = effs[cpt];
     }
     int best_cpt = 0, best_nt = 0;
-    for (int cpt = 1; cpt <= 3; ++cpt)
+    for (int cpt = 1; cpt <= 4; ++cpt)
         if (nts[cpt] && effs[cpt] >= best - 0.02) {
             best_cpt = cpt;
             best_nt = nts[cpt];
@@ -69,12 +67,17 @@ fhr_status pass_config(fhr_ctx *ctx, int K, int Nk, int ldP, int p_dtype, PassCo
     cfg->cpt = best_cpt;
     cfg->nt = best_nt;
     const size_t stage = (size_t)kPassRows * ldP * esize;
-    const size_t budget = (size_t)ctx->max_smem_optin;
-    int stages = 4;
-    while (stages > 2 && pass_smem(K, best_nt, ldP, esize, stages) > budget) --stages;
-    if (pass_smem(K, best_nt, ldP, esize, stages) > budget)
+    // two CTAs per SM when the ring fits half of the SM's shared memory
+    // (each SM has ~228 KB; a CTA may use up to max_smem_optin)
+    const size_t half = (size_t)ctx->max_smem_optin / 2 - 1024;
+    int stages = 6;
+    while (stages > 3 && pass_smem(K, best_nt, ldP, esize, stages) > half) --stages;
+    if (pass_smem(K, best_nt, ldP, esize, stages) > half) {
+        stages = 6;
+        while (stages > 2 && pass_smem(K, best_nt, ldP, esize, stages) > (size_t)ctx->max_smem_optin) --stages;
+    }
+    if (pass_smem(K, best_nt, ldP, esize, stages) > (size_t)ctx->max_smem_optin)
         return set_error(ctx, FHR_ERR_UNSUPPORTED, "Nk too large: a %zu-byte tile does not fit shared memory", stage);
-    // prefer more resident CTAs over deeper rings when tiles are small
     cfg->stages = stages;
     cfg->smem = pass_smem(K, best_nt, ldP, esize, stages);
     const void *fn = p_dtype == FHR_BF16 ? (const void *)pick<__nv_bfloat16>(K, best_cpt)
@@ -82,7 +85,7 @@ fhr_status pass_config(fhr_ctx *ctx, int K, int Nk, int ldP, int p_dtype, PassCo
     if (!fn) return set_error(ctx, FHR_ERR_UNSUPPORTED, "no pass kernel for K=%d", K);
     FHR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg->smem));
     int per_sm = 0;
-    FHR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, best_nt + 32, cfg->smem));
+    FHR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, best_nt + 64, cfg->smem));
     if (per_sm < 1) return set_error(ctx, FHR_ERR_UNSUPPORTED, "fused pass does not fit on an SM");
     cfg->grid = ctx->sm_count * per_sm;
     cfg->fn = fn;
@@ -93,7 +96,7 @@ fhr_status launch_pass(fhr_ctx *ctx, const PassConfig &cfg, const PassArgs &a) {
     PassArgs b = a;
     b.stages = cfg.stages;
     void *args[] = {&b};
-    FHR_TIMED(TM_NMF_PASS, cudaLaunchKernel(cfg.fn, dim3(cfg.grid), dim3(cfg.nt + 32), args, cfg.smem, ctx->stream));
+    FHR_TIMED(TM_NMF_PASS, cudaLaunchKernel(cfg.fn, dim3(cfg.grid), dim3(cfg.nt + 64), args, cfg.smem, ctx->stream));
     return FHR_OK;
 }
 

@@ -325,7 +325,7 @@ int nndsvd_L(int K, int Nk) { return std::min(std::min(kMaxK, K + 3), Nk); }
 
 // reduction kernel shared with the decomposition
 __global__ void nmf_reduce(const float *Qpart, const float *Gpart, const float *ssqpart, int grid, int nval, int K,
-                           double *Q64, double *GW64, double *ssq64);
+                           double *Q64, double *GW64, double *ssq64, int want_ssq);
 
 fhr_status nndsvd_run(fhr_ctx *ctx, const fhr_nmf_params *p, const void *P, float *D, float *W, void *region,
                       int *status) {
@@ -358,6 +358,7 @@ fhr_status nndsvd_run(fhr_ctx *ctx, const fhr_nmf_params *p, const void *P, floa
     a.Gpart = w.Gpart;
     a.ssqpart = w.ssqpart;
     a.status = status;
+    a.want_ssq = 0;
 
     auto orthonormalise = [&](void) -> fhr_status {
         for (int round = 0; round < 2; ++round) {   // Cholesky-QR twice
@@ -378,7 +379,7 @@ fhr_status nndsvd_run(fhr_ctx *ctx, const fhr_nmf_params *p, const void *P, floa
         a.mode = PASS_PROJECT;
         FHR_TRY(launch_pass(ctx, cfgL, a));
         nmf_reduce<<<(unsigned)cdiv(nval, 32) + 1, 256, 0, st>>>(w.Qpart, w.Gpart, w.ssqpart, cfgL.grid, nval, L,
-                                                                 w.Z64, w.H64, w.ssq64);
+                                                                 w.Z64, w.H64, w.ssq64, 0);
         FHR_LAUNCHED();
         if (it < q) FHR_TRY(orthonormalise());
     }

@@ -1,0 +1,35 @@
+"""Small, fixed cases for profiling single kernels (ncu captures must stay small).
+
+    python -m paper_2410_22500_gb300.profcase nmf_pass [Np]
+
+`nmf_pass`: P of Np x 1200 uniform f32 (default Np = 92,160: 442 MB, larger than
+L2), K = 5, three fast-HALS iterations from a fixed start.  Launch 0 is the first
+pass; profile with `-k regex:nmf_pass -s 1 -c 1`.
+"""
+import sys
+
+import torch
+
+from . import build, fhr
+
+
+def nmf_pass(Np: int = 92160, Nk: int = 1200, K: int = 5, iters: int = 3) -> None:
+    build.build()
+    ctx = fhr.Context(0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    P = torch.rand((Np, Nk), device="cuda", generator=g)
+    D = torch.rand((Nk, K), device="cuda", generator=g) + 0.1
+    W = torch.rand((Np, K), device="cuda", generator=g) + 0.1
+    ctx.decompose(P, Nk, K, iters, D=D, W=W)
+    torch.cuda.synchronize()
+    ctx.close()
+    print("ok")
+
+
+if __name__ == "__main__":
+    case = sys.argv[1] if len(sys.argv) > 1 else "nmf_pass"
+    if case == "nmf_pass":
+        nmf_pass(int(sys.argv[2]) if len(sys.argv) > 2 else 92160)
+    else:
+        raise SystemExit("unknown case %r" % case)
