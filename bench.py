@@ -203,8 +203,8 @@ def run_ours(args, rank, world, device):
     ms = ev0.elapsed_time(ev1)
     launches, _ = ctx.profile_read()
     pass_n, pass_ms = ctx.profile_read("nmf_pass")
-    fams = {n: ctx.profile_read(n) for n in ("normalise", "nmf_pass", "nmf_reduce", "nmf_update", "proj_fwd",
-                                             "mbir_update", "expand")}
+    fams = {n: ctx.profile_read(n) for n in ("normalise", "nndsvd_pass", "nmf_pass", "nmf_reduce", "nmf_update",
+                                             "proj_fwd", "mbir_update", "expand")}
     ctx.profile(False)
     clk = clocks.stop()
     if ctx.status(ws) != 0:

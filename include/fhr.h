@@ -75,9 +75,12 @@ const char *fhr_version(void);
  * kernel families with CUDA events on the context's stream (host-side event
  * objects; no device memory).  fhr_profile_read(ctx, name, ...) synchronises
  * those events and returns the number of launches and their summed device
- * time in ms for `name` in {"normalise", "nmf_pass", "nmf_reduce",
- * "nmf_update", "proj_fwd", "mbir_update", "proj_bwd", "expand"}; with
- * name == NULL it returns the total launch count since the last enable. */
+ * time in ms for `name` in {"normalise", "nmf_pass", "nndsvd_pass",
+ * "nmf_reduce", "nmf_update", "proj_fwd", "mbir_update", "proj_bwd",
+ * "expand"}; with
+ * name == NULL it returns the total launch count since the last enable.
+ * "nmf_pass" counts the fused passes of the HALS iterations; the projection
+ * passes of the NNDSVD start are counted under "nndsvd_pass". */
 fhr_status fhr_profile_enable(fhr_ctx *ctx, int enable);
 fhr_status fhr_profile_read(fhr_ctx *ctx, const char *name, long long *launches, double *ms);
 
@@ -134,7 +137,7 @@ typedef struct {
     int iters;
     int init;
     int p_dtype;
-    int power_iters;   /* subspace iterations for NNDSVD (default 12 when 0) */
+    int power_iters;   /* subspace iterations for NNDSVD (default 8 when 0) */
     uint64_t seed;
 } fhr_nmf_params;
 

@@ -36,8 +36,8 @@ cudaEvent_t *timer_begin(fhr_ctx *ctx, int id) {
     return e;
 }
 
-static const char *kTimerNames[TM_COUNT] = {"normalise", "nmf_pass", "nmf_reduce", "nmf_update",
-                                            "proj_fwd", "mbir_update", "proj_bwd", "expand"};
+static const char *kTimerNames[TM_COUNT] = {"normalise", "nmf_pass", "nmf_reduce", "nmf_update", "proj_fwd",
+                                            "mbir_update", "proj_bwd", "expand", "nndsvd_pass"};
 
 }  // namespace fhr
 

@@ -32,7 +32,7 @@ static size_t carve_nmf(void *base, int64_t Np, int Nk, int K, int grid, int ite
     t.ssq64 = c.take<double>(1);
     t.D64 = c.take<double>((size_t)Nk * K);
     const int nb = (int)cdiv(Nk, kUpdThreads);
-    t.Bpart = c.take<double>((size_t)nb * (K + 1 + K * K));
+    t.Bpart = c.take<double>((size_t)nb * (K + 1 + K * (K + 1) / 2));
     t.objscratch = c.take<double>((size_t)(iters > 0 ? iters : 1));
     (void)Np;
     if (w) *w = t;
@@ -120,18 +120,25 @@ __global__ void nmf_reduce(const float *Qpart, const float *Gpart, const float *
 // D half-step of fast HALS for bin k (one thread per bin), FP64:
 //   d_ks <- max(0, d_ks + (Q_ks - sum_t d_kt GW_ts) / GW_ss)
 // then the last block normalises the columns, evaluates the objective and
-// publishes the state for the next pass.
+// publishes the state for the next pass.  Per-bin contributions to the column
+// norms, <D, Q> and D^T D (upper triangle) are summed in fixed order: through
+// shared memory inside a block, over blocks in the last block.
+constexpr int kUpdNV = kMaxK + 1 + kMaxK * (kMaxK + 1) / 2;   // values reduced per bin (max)
+
 __global__ void nmf_update_d(const double *Q64, const double *GW64, const double *ssq64, double *D64, int Nk,
                              int K, const NmfState *st_in, NmfState *st_out, double *Bpart,
                              unsigned int *counter, double *obj, int *status) {
     __shared__ double gw[kMaxK * kMaxK];
-    __shared__ double red[kUpdThreads];
+    __shared__ double invh[kMaxK];
+    __shared__ double vals[kUpdThreads][kUpdNV + 1];
     __shared__ bool last;
     const int tid = threadIdx.x;
     const int k = blockIdx.x * blockDim.x + tid;
+    const int nv = K + 1 + K * (K + 1) / 2;
     if (tid < K * K) gw[tid] = GW64[tid];
     __syncthreads();
-    const int nv = K + 1 + K * K;
+    if (tid < K) invh[tid] = gw[tid * K + tid] != 0.0 ? 1.0 / gw[tid * K + tid] : 0.0;
+    __syncthreads();
     double d[kMaxK], q[kMaxK];
 #pragma unroll
     for (int s = 0; s < kMaxK; ++s) d[s] = q[s] = 0.0;
@@ -141,48 +148,56 @@ __global__ void nmf_update_d(const double *Q64, const double *GW64, const double
             q[s] = Q64[(size_t)k * K + s];
         }
         for (int s = 0; s < K; ++s) {
-            const double h = gw[s * K + s];
-            if (h == 0.0) continue;
+            if (invh[s] == 0.0) continue;
             double g = q[s];
             for (int t = 0; t < K; ++t) g -= d[t] * gw[t * K + s];
-            d[s] = fmax(0.0, d[s] + g / h);
+            d[s] = fmax(0.0, d[s] + g * invh[s]);
         }
         for (int s = 0; s < K; ++s) D64[(size_t)k * K + s] = d[s];
     }
-    // block partials of sum d^2 (per column), <d, q>, d d^T
-    for (int v = 0; v < nv; ++v) {
-        double x;
-        if (v < K) x = d[v] * d[v];
-        else if (v == K) {
-            x = 0.0;
-            for (int s = 0; s < K; ++s) x += d[s] * q[s];
-        } else {
-            const int p = v - K - 1;
-            x = d[p / K] * d[p % K];
+    // this bin's contributions: d_s^2 (K), <d, q> (1), d_s d_t for t >= s
+    {
+        double *v = vals[tid];
+        double dq = 0.0;
+        for (int s = 0; s < K; ++s) {
+            v[s] = d[s] * d[s];
+            dq += d[s] * q[s];
         }
-        red[tid] = x;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (tid < o) red[tid] += red[tid + o];
-            __syncthreads();
-        }
-        if (tid == 0) Bpart[(size_t)blockIdx.x * nv + v] = red[0];
-        __syncthreads();
+        v[K] = dq;
+        int o = K + 1;
+        for (int s = 0; s < K; ++s)
+            for (int t = s; t < K; ++t) v[o++] = d[s] * d[t];
+    }
+    __syncthreads();
+    if (tid < nv) {
+        double a = 0.0;
+        for (int i = 0; i < (int)blockDim.x; ++i) a += vals[i][tid];
+        Bpart[(size_t)blockIdx.x * nv + tid] = a;
     }
     __threadfence();
+    __syncthreads();
     if (tid == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
+    __shared__ double tot[kUpdNV];
+    if (tid < nv) {
+        double a = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) a += Bpart[(size_t)b * nv + tid];
+        tot[tid] = a;
+    }
+    __syncthreads();
     if (tid == 0) {
-        double dd[kMaxK], dq = 0.0, dtd[kMaxK * kMaxK];
-        for (int v = 0; v < nv; ++v) {
-            double a = 0.0;
-            for (unsigned b = 0; b < gridDim.x; ++b) a += Bpart[(size_t)b * nv + v];
-            if (v < K) dd[v] = a;
-            else if (v == K) dq = a;
-            else dtd[v - K - 1] = a;
-        }
+        double dd[kMaxK], dtd[kMaxK * kMaxK];
+        for (int s = 0; s < K; ++s) dd[s] = tot[s];
+        const double dq = tot[K];
+        int o = K + 1;
+        for (int s = 0; s < K; ++s)
+            for (int t = s; t < K; ++t) {
+                dtd[s * K + t] = tot[o];
+                dtd[t * K + s] = tot[o];
+                ++o;
+            }
         double f = *ssq64 - 2.0 * dq;
         for (int i = 0; i < K * K; ++i) f += dtd[i] * gw[i];
         *obj = f;

@@ -96,7 +96,8 @@ fhr_status launch_pass(fhr_ctx *ctx, const PassConfig &cfg, const PassArgs &a) {
     PassArgs b = a;
     b.stages = cfg.stages;
     void *args[] = {&b};
-    FHR_TIMED(TM_NMF_PASS, cudaLaunchKernel(cfg.fn, dim3(cfg.grid), dim3(cfg.nt + 64), args, cfg.smem, ctx->stream));
+    FHR_TIMED(a.mode == PASS_HALS ? TM_NMF_PASS : TM_NNDSVD_PASS,
+              cudaLaunchKernel(cfg.fn, dim3(cfg.grid), dim3(cfg.nt + 64), args, cfg.smem, ctx->stream));
     return FHR_OK;
 }
 

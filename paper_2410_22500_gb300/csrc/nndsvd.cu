@@ -321,7 +321,7 @@ size_t carve_nndsvd(Carve &c, int64_t Np, int Nk, int L, int K, int grid, void *
     return c.size();
 }
 
-int nndsvd_L(int K, int Nk) { return std::min(std::min(kMaxK, K + 3), Nk); }
+int nndsvd_L(int K, int Nk) { return std::min(std::min(kMaxK, K + 2), Nk); }
 
 // reduction kernel shared with the decomposition
 __global__ void nmf_reduce(const float *Qpart, const float *Gpart, const float *ssqpart, int grid, int nval, int K,
@@ -340,7 +340,7 @@ fhr_status nndsvd_run(fhr_ctx *ctx, const fhr_nmf_params *p, const void *P, floa
     cudaStream_t st = ctx->stream;
     FHR_CUDA(cudaMemsetAsync(w.counter, 0, 4 * sizeof(unsigned), st));
     const int nb = (int)cdiv(Nk, kColThreads);
-    const int q = p->power_iters > 0 ? p->power_iters : 12;
+    const int q = p->power_iters > 0 ? p->power_iters : 8;
 
     nn_random<<<(unsigned)cdiv((int64_t)Nk * L, 256), 256, 0, st>>>(w.Z64, Nk, L, p->seed);
     FHR_LAUNCHED();
