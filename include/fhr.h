@@ -123,6 +123,11 @@ fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *prm,
  *         FHR_INIT_NNDSVD: NNDSVD start (Sec. III) from a randomised
  *         subspace iteration for the top-K singular vectors of P, seeded
  *         by `seed` (counter-based generator, splitmix64).
+ *         FHR_INIT_LEARNED (an added form, not in the paper): W0 = MLP(p_j)
+ *         for every pixel (mlp, mlp_params; mlp->K == K, mlp->Nk == Nk,
+ *         mlp->ldx == ldP, mlp->x_dtype == p_dtype), one pass with W0 fixed
+ *         for P^T W0 and W0^T W0, then D0 from ten HALS D half-steps from
+ *         D = 0; the iterations then run as from a GIVEN start.
  *   P     [Np][ldP] in p_dtype; D [Nk][K] and W [Np][K] float, in/out.
  *   obj   device double [iters] or NULL: ||p - V D^T||^2 after each
  *         iteration, from the Gram identity in double precision.
@@ -130,6 +135,9 @@ fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *prm,
  * ---------------------------------------------------------------------- */
 #define FHR_INIT_GIVEN 0
 #define FHR_INIT_NNDSVD 1
+#define FHR_INIT_LEARNED 2
+
+struct fhr_mlp_dims_s;
 
 typedef struct {
     int64_t Np;
@@ -139,6 +147,9 @@ typedef struct {
     int p_dtype;
     int power_iters;   /* subspace iterations for NNDSVD (default 8 when 0) */
     uint64_t seed;
+    /* FHR_INIT_LEARNED only: the warm-start network (see fhr_mlp_forward) */
+    const struct fhr_mlp_dims_s *mlp;
+    const float *mlp_params;
 } fhr_nmf_params;
 
 fhr_status fhr_decompose_workspace_size(fhr_ctx *ctx, const fhr_nmf_params *prm, size_t *bytes);
@@ -227,6 +238,41 @@ fhr_status fhr_reconstruct(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_param
  * ---------------------------------------------------------------------- */
 fhr_status fhr_expand(fhr_ctx *ctx, int N, int Nr, int K, int Nk, int k0, int k1,
                       const float *xs, const float *D, int xh_dtype, void *xh);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start (not in the paper; an added form of the decomposition's
+ * start).  A 3-layer MLP maps a pixel's spectrum p (Nk bins) to K nonnegative
+ * subspace coefficients:
+ *   a1 = gelu(W1 p + b1), a2 = gelu(W2 a1 + b2), y = softplus(W3 a2 + b3),
+ * gelu exact (erf form), softplus(z) = log(1 + e^z) (z for z > 20).
+ * Parameters: one FP32 array [W1 (H1 x Nk), b1 (H1), W2 (H2 x H1), b2 (H2),
+ * W3 (K x H2), b3 (K)], weights row-major [out][in].  FP32 accumulation
+ * throughout; with weights_bf16 the weights and the hidden activations are
+ * rounded to bf16 (round to nearest even) before each contraction.
+ * Inputs X: [M][ldx] rows in x_dtype (FHR_F32 or FHR_BF16), e.g. rows of P.
+ * ---------------------------------------------------------------------- */
+typedef struct fhr_mlp_dims_s {
+    int Nk, H1, H2, K;
+    int ldx;
+    int x_dtype;
+    int weights_bf16;
+} fhr_mlp_dims;
+
+/* Workspace for fhr_mlp_forward (train = 0) or fhr_mlp_grad (train = 1). */
+fhr_status fhr_mlp_workspace_size(fhr_ctx *ctx, const fhr_mlp_dims *dims, int train, size_t *bytes);
+/* Y [M][K] float = MLP(X) for any M (processed in chunks of 32768 rows). */
+fhr_status fhr_mlp_forward(fhr_ctx *ctx, const fhr_mlp_dims *dims, const float *params, int64_t M,
+                           const void *X, float *Y, void *ws, size_t ws_bytes);
+/* Mean-squared error against T [M][K] (loss, a device double, may be NULL)
+ * and its gradient with respect to every parameter (grad: same layout as
+ * params, overwritten).  1 <= M <= 32768 rows per call. */
+fhr_status fhr_mlp_grad(fhr_ctx *ctx, const fhr_mlp_dims *dims, const float *params, int64_t M,
+                        const void *X, const float *T, float *grad, double *loss, void *ws, size_t ws_bytes);
+/* One AdamW step (decoupled weight decay) on n parameters, step >= 1:
+ * m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * w -= lr ((m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps) + weight_decay w). */
+fhr_status fhr_mlp_adamw(fhr_ctx *ctx, int64_t n, float *params, const float *grad, float *m, float *v,
+                         int step, float lr, float beta1, float beta2, float eps, float weight_decay);
 
 /* ------------------------------------------------------------------------
  * Algorithm 1 end to end: normalise -> decompose -> reconstruct -> expand.

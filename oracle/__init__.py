@@ -13,6 +13,8 @@ Every function cites the passage of the paper it follows.  Parity status:
   projector        pinned (polygon clipping, adjointness, mass, disk chords)
   MBIR (SQS)       pinned (dense least squares, quadratic prior solve, monotone)
   expansion        pinned (identity dictionary, commutes with the projector)
+  MLP warm start   pinned (closed-form activations, layer-wise numpy, central
+                   differences of the loss, AdamW closed form)
 """
 from __future__ import annotations
 
@@ -308,3 +310,59 @@ def fhr_pipeline(y, y0, K, N, theta, *, nmf_iters=200, mbir_iters=20, dead=None,
     xs = mbir(V, N, Nr, K, theta, sv, sx, p=p, T=T, iters=mbir_iters, momentum=momentum)
     xh = expand(xs, D, N, Nr)
     return dict(P=P, D0=D0, W0=W0, D=D, W=W, obj=obj, sv=sv, sx=sx, xs=xs, xh=xh)
+
+
+# ---------------------------------------------------------------- learned warm start (MLP)
+def _mlp_lib():
+    L = lib()
+    if not getattr(L, "_mlp_ready", False):
+        L.or_gelu.restype = ctypes.c_double
+        L.or_gelu.argtypes = [ctypes.c_double]
+        L.or_softplus.restype = ctypes.c_double
+        L.or_softplus.argtypes = [ctypes.c_double]
+        L.or_mlp_nparams.restype = ctypes.c_long
+        L.or_mlp_nparams.argtypes = [ctypes.c_int] * 4
+        L.or_mlp_forward.restype = ctypes.c_double
+        L.or_mlp_forward.argtypes = [ctypes.c_int] * 5 + [_dp, _dp, _dp, _dp]
+        L.or_mlp_grad.restype = ctypes.c_double
+        L.or_mlp_grad.argtypes = [ctypes.c_int] * 5 + [_dp, _dp, _dp, _dp]
+        L.or_adamw.argtypes = [ctypes.c_long, _dp, _dp, _dp, _dp, ctypes.c_int] + [ctypes.c_double] * 5
+        L._mlp_ready = True
+    return L
+
+
+def gelu(x):
+    return _mlp_lib().or_gelu(x)
+
+
+def softplus(z):
+    return _mlp_lib().or_softplus(z)
+
+
+def mlp_nparams(Nk, H1, H2, K):
+    return _mlp_lib().or_mlp_nparams(Nk, H1, H2, K)
+
+
+def mlp_forward(prm, X, dims, T=None):
+    """MLP spectrum -> coefficients (the library's learned warm start). Returns Y [M][K] (and the MSE loss)."""
+    Nk, H1, H2, K = dims
+    X = _f64(X).reshape(-1, Nk)
+    Y = np.empty((X.shape[0], K))
+    loss = _mlp_lib().or_mlp_forward(X.shape[0], Nk, H1, H2, K, _d(_f64(prm)), _d(X), _d(Y),
+                                     None if T is None else _d(_f64(T)))
+    return (Y, loss) if T is not None else Y
+
+
+def mlp_grad(prm, X, T, dims):
+    """Mean-squared-error loss and its gradient with respect to the packed parameters."""
+    Nk, H1, H2, K = dims
+    X = _f64(X).reshape(-1, Nk)
+    G = np.empty(mlp_nparams(Nk, H1, H2, K))
+    loss = _mlp_lib().or_mlp_grad(X.shape[0], Nk, H1, H2, K, _d(_f64(prm)), _d(X), _d(_f64(T)), _d(G))
+    return loss, G
+
+
+def adamw(w, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, wd=1e-4):
+    """One AdamW step in place (decoupled weight decay)."""
+    _mlp_lib().or_adamw(w.size, _d(w), _d(_f64(g)), _d(m), _d(v), t, lr, b1, b2, eps, wd)
+    return w

@@ -20,6 +20,7 @@
  *   sinogram   [Nv][Nc][Wl]  (equal to W viewed with Wl = Nr*K)
  *   x^h        [Nr][N][N][Nk]
  */
+#define _GNU_SOURCE
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -564,4 +565,145 @@ void or_expand(int N, int Nr, int K, int Nk, const double *xs, const double *D, 
                     o[k] = s;
                 }
             }
+}
+
+/* ------------------------------------------------------------------------
+ * Learned warm start (not in the paper; the library's added form): a
+ * 3-layer MLP mapping a pixel's Nk-bin spectrum p to K nonnegative subspace
+ * coefficients, trained by mean-squared error against coefficients that the
+ * plain method produced.
+ *   z1 = W1 p + b1,  a1 = gelu(z1)          (H1 units)
+ *   z2 = W2 a1 + b2, a2 = gelu(z2)          (H2 units)
+ *   z3 = W3 a2 + b3, y = softplus(z3)       (K outputs)
+ * gelu(x) = x Phi(x) (exact, erf form); softplus(z) = log(1 + e^z), z for z > 20.
+ * loss = mean over the M pixels and K outputs of (y - t)^2.
+ * Parameters are packed [W1 (H1 x Nk), b1, W2 (H2 x H1), b2, W3 (K x H2), b3],
+ * weights row-major [out][in].
+ * ---------------------------------------------------------------------- */
+static double gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+static double gelu_d(double x)
+{
+    const double phi = exp(-0.5 * x * x) / sqrt(2.0 * M_PI);
+    return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * phi;
+}
+static double softplus(double z) { return z > 20.0 ? z : log1p(exp(z)); }
+static double sigmoid(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+double or_gelu(double x) { return gelu(x); }
+double or_softplus(double z) { return softplus(z); }
+
+long or_mlp_nparams(int Nk, int H1, int H2, int K)
+{
+    return (long)H1 * Nk + H1 + (long)H2 * H1 + H2 + (long)K * H2 + K;
+}
+
+/* forward for M pixels; Y [M][K]; returns the loss if T != NULL */
+double or_mlp_forward(int M, int Nk, int H1, int H2, int K, const double *prm, const double *X,
+                      double *Y, const double *T)
+{
+    const double *W1 = prm, *b1 = W1 + (long)H1 * Nk, *W2 = b1 + H1, *b2 = W2 + (long)H2 * H1;
+    const double *W3 = b2 + H2, *b3 = W3 + (long)K * H2;
+    double *a1 = (double *)malloc(sizeof(double) * H1), *a2 = (double *)malloc(sizeof(double) * H2);
+    double loss = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const double *x = X + (long)m * Nk;
+        for (int j = 0; j < H1; ++j) {
+            double z = b1[j];
+            for (int k = 0; k < Nk; ++k) z += W1[(long)j * Nk + k] * x[k];
+            a1[j] = gelu(z);
+        }
+        for (int j = 0; j < H2; ++j) {
+            double z = b2[j];
+            for (int k = 0; k < H1; ++k) z += W2[(long)j * H1 + k] * a1[k];
+            a2[j] = gelu(z);
+        }
+        for (int j = 0; j < K; ++j) {
+            double z = b3[j];
+            for (int k = 0; k < H2; ++k) z += W3[(long)j * H2 + k] * a2[k];
+            double y = softplus(z);
+            Y[(long)m * K + j] = y;
+            if (T) loss += (y - T[(long)m * K + j]) * (y - T[(long)m * K + j]);
+        }
+    }
+    free(a1);
+    free(a2);
+    return T ? loss / ((double)M * K) : 0.0;
+}
+
+/* loss and its gradient with respect to every packed parameter (G, same layout) */
+double or_mlp_grad(int M, int Nk, int H1, int H2, int K, const double *prm, const double *X,
+                   const double *T, double *G)
+{
+    const double *W1 = prm, *b1 = W1 + (long)H1 * Nk, *W2 = b1 + H1, *b2 = W2 + (long)H2 * H1;
+    const double *W3 = b2 + H2, *b3 = W3 + (long)K * H2;
+    long np = or_mlp_nparams(Nk, H1, H2, K);
+    memset(G, 0, sizeof(double) * np);
+    double *gW1 = G, *gb1 = gW1 + (long)H1 * Nk, *gW2 = gb1 + H1, *gb2 = gW2 + (long)H2 * H1;
+    double *gW3 = gb2 + H2, *gb3 = gW3 + (long)K * H2;
+    double *z1 = (double *)malloc(sizeof(double) * H1), *a1 = (double *)malloc(sizeof(double) * H1);
+    double *z2 = (double *)malloc(sizeof(double) * H2), *a2 = (double *)malloc(sizeof(double) * H2);
+    double *d1 = (double *)malloc(sizeof(double) * H1), *d2 = (double *)malloc(sizeof(double) * H2);
+    double *d3 = (double *)malloc(sizeof(double) * K);
+    double loss = 0.0, scale = 2.0 / ((double)M * K);
+    for (int m = 0; m < M; ++m) {
+        const double *x = X + (long)m * Nk;
+        for (int j = 0; j < H1; ++j) {
+            double z = b1[j];
+            for (int k = 0; k < Nk; ++k) z += W1[(long)j * Nk + k] * x[k];
+            z1[j] = z;
+            a1[j] = gelu(z);
+        }
+        for (int j = 0; j < H2; ++j) {
+            double z = b2[j];
+            for (int k = 0; k < H1; ++k) z += W2[(long)j * H1 + k] * a1[k];
+            z2[j] = z;
+            a2[j] = gelu(z);
+        }
+        for (int j = 0; j < K; ++j) {
+            double z = b3[j];
+            for (int k = 0; k < H2; ++k) z += W3[(long)j * H2 + k] * a2[k];
+            double y = softplus(z), e = y - T[(long)m * K + j];
+            loss += e * e;
+            d3[j] = scale * e * sigmoid(z);          /* d loss / d z3 */
+        }
+        for (int k = 0; k < H2; ++k) {
+            double s = 0.0;
+            for (int j = 0; j < K; ++j) s += W3[(long)j * H2 + k] * d3[j];
+            d2[k] = s * gelu_d(z2[k]);               /* d loss / d z2 */
+        }
+        for (int k = 0; k < H1; ++k) {
+            double s = 0.0;
+            for (int j = 0; j < H2; ++j) s += W2[(long)j * H1 + k] * d2[j];
+            d1[k] = s * gelu_d(z1[k]);               /* d loss / d z1 */
+        }
+        for (int j = 0; j < K; ++j) {
+            gb3[j] += d3[j];
+            for (int k = 0; k < H2; ++k) gW3[(long)j * H2 + k] += d3[j] * a2[k];
+        }
+        for (int j = 0; j < H2; ++j) {
+            gb2[j] += d2[j];
+            for (int k = 0; k < H1; ++k) gW2[(long)j * H1 + k] += d2[j] * a1[k];
+        }
+        for (int j = 0; j < H1; ++j) {
+            gb1[j] += d1[j];
+            for (int k = 0; k < Nk; ++k) gW1[(long)j * Nk + k] += d1[j] * x[k];
+        }
+    }
+    free(z1); free(a1); free(z2); free(a2); free(d1); free(d2); free(d3);
+    return loss / ((double)M * K);
+}
+
+/* AdamW (decoupled weight decay), step t >= 1:
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   w -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps) + lr wd w */
+void or_adamw(long n, double *w, const double *g, double *m, double *v, int t, double lr, double b1,
+              double b2, double eps, double wd)
+{
+    double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+    for (long i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        double mh = m[i] / c1, vh = v[i] / c2;
+        w[i] -= lr * (mh / (sqrt(vh) + eps) + wd * w[i]);
+    }
 }

@@ -1,0 +1,491 @@
+// Learned warm start: a 3-layer MLP (Nk -> H1 -> H2 -> K, GELU, GELU,
+// softplus) mapping a pixel's spectrum to K nonnegative subspace
+// coefficients, with hand-written forward, backward and AdamW kernels.
+// Not in the paper: an added form that starts the fast-HALS iterations of
+// Sec. III closer to their end point.
+//
+// Every layer is one tiled GEMM with a fused epilogue (bias + activation, or
+// the activation's derivative); weight gradients are split-K GEMMs over the
+// pixel dimension with a fixed-order reduction of the splits.  Arithmetic is
+// FP32 (FP32 accumulation); with weights_bf16 the weights and the hidden
+// activations that feed the next layer are rounded to bf16.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace fhr {
+
+enum GemmEpi { EPI_STORE = 0, EPI_BIAS_GELU, EPI_BIAS_SOFTPLUS, EPI_GELU_BACK };
+
+struct GemmArgs {
+    int M, N, Kd;
+    const void *A;
+    int64_t sai, sak;   // A(i, k) = A[i * sai + k * sak]
+    const void *B;
+    int64_t sbk, sbj;   // B(k, j) = B[k * sbk + j * sbj]
+    float *C;           // C[i * ldc + j] (+ split * split_stride)
+    int64_t ldc, split_stride;
+    void *C2;           // activation output (EPI_BIAS_GELU), f32 or bf16
+    int c2_bf16;
+    int64_t ldc2;
+    const float *bias;
+    const float *Z;     // pre-activation for EPI_GELU_BACK
+    int64_t ldz;
+    int kchunk;         // contraction range per grid.z slice
+};
+
+template <typename T>
+__device__ __forceinline__ float ld_as_f32(const void *p, int64_t i);
+template <>
+__device__ __forceinline__ float ld_as_f32<float>(const void *p, int64_t i) {
+    return __ldg(reinterpret_cast<const float *>(p) + i);
+}
+template <>
+__device__ __forceinline__ float ld_as_f32<__nv_bfloat16>(const void *p, int64_t i) {
+    return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(p)[i]);
+}
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d_f(float x) {
+    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+}
+__device__ __forceinline__ float softplus_f(float z) { return z > 20.f ? z : log1pf(expf(z)); }
+__device__ __forceinline__ float sigmoid_f(float z) { return 1.f / (1.f + expf(-z)); }
+
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+template <typename TA, typename TB, int EPI>
+__global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
+    __shared__ __align__(16) float As[GBK][GBM];
+    __shared__ __align__(16) float Bs[GBK][GBN];
+    const int tid = threadIdx.x;
+    const int i0 = blockIdx.y * GBM, j0 = blockIdx.x * GBN;
+    const int kbeg = blockIdx.z * g.kchunk;
+    const int kend = min(g.Kd, kbeg + g.kchunk);
+    const int ty = tid / 16, tx = tid % 16;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    const bool a_kfast = g.sak == 1;
+    const bool b_jfast = g.sbj == 1;
+    for (int k0 = kbeg; k0 < kend; k0 += GBK) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            int i, k;
+            if (a_kfast) {
+                i = tid / 4;
+                k = (tid % 4) * 4 + e;
+            } else {
+                k = tid / 16;
+                i = (tid % 16) * 4 + e;
+            }
+            const int gi = i0 + i, gk = k0 + k;
+            As[k][i] = (gi < g.M && gk < kend) ? ld_as_f32<TA>(g.A, (int64_t)gi * g.sai + (int64_t)gk * g.sak) : 0.f;
+            int j, kb;
+            if (b_jfast) {
+                kb = tid / 16;
+                j = (tid % 16) * 4 + e;
+            } else {
+                j = tid / 4;
+                kb = (tid % 4) * 4 + e;
+            }
+            const int gj = j0 + j, gkb = k0 + kb;
+            Bs[kb][j] = (gj < g.N && gkb < kend) ? ld_as_f32<TB>(g.B, (int64_t)gkb * g.sbk + (int64_t)gj * g.sbj) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GBK; ++k) {
+            const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(av[p], bv[q], acc[p][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int i = i0 + ty * 4 + p;
+        if (i >= g.M) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + tx * 4 + q;
+            if (j >= g.N) continue;
+            float v = acc[p][q];
+            if (EPI == EPI_STORE) {
+                g.C[(int64_t)blockIdx.z * g.split_stride + (int64_t)i * g.ldc + j] = v;
+            } else if (EPI == EPI_BIAS_GELU) {
+                v += g.bias[j];
+                if (g.C) g.C[(int64_t)i * g.ldc + j] = v;
+                const float a = gelu_f(v);
+                if (g.c2_bf16)
+                    reinterpret_cast<__nv_bfloat16 *>(g.C2)[(int64_t)i * g.ldc2 + j] = __float2bfloat16_rn(a);
+                else
+                    reinterpret_cast<float *>(g.C2)[(int64_t)i * g.ldc2 + j] = a;
+            } else if (EPI == EPI_BIAS_SOFTPLUS) {
+                v += g.bias[j];
+                if (g.C2) reinterpret_cast<float *>(g.C2)[(int64_t)i * g.ldc2 + j] = v;
+                g.C[(int64_t)i * g.ldc + j] = softplus_f(v);
+            } else {   // EPI_GELU_BACK: dZ = (dA) * gelu'(Z)
+                g.C[(int64_t)i * g.ldc + j] = v * gelu_d_f(g.Z[(int64_t)i * g.ldz + j]);
+            }
+        }
+    }
+}
+
+// loss partials and dZ3 = 2/(M K) (y - t) sigmoid(z3), one thread per output
+__global__ void mlp_loss_kernel(const float *Y, const float *Z3, const float *T, int64_t n, float scale, float *dZ3,
+                                double *part) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float e = Y[i] - T[i];
+        s += (double)e * (double)e;
+        dZ3[i] = scale * e * sigmoid_f(Z3[i]);
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void mlp_loss_final(const double *part, int nb, double inv_n, double *loss) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0.0;
+        for (int b = 0; b < nb; ++b) a += part[b];
+        *loss = a * inv_n;
+    }
+}
+
+// grad[o + j] = sum over splits of partials (fixed order); bias grads = column sums of dZ
+__global__ void mlp_reduce_splits(const float *part, int splits, int64_t n, float *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float a = 0.f;
+        for (int s = 0; s < splits; ++s) a += part[(int64_t)s * n + i];
+        out[i] = a;
+    }
+}
+
+__global__ void mlp_colsum(const float *dZ, int64_t M, int N, float *out) {
+    // one block per column chunk of 32, threads over rows; fixed-order tree
+    __shared__ float sh[8][33];
+    const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int r = threadIdx.x >> 5;
+    float a = 0.f;
+    if (j < N)
+        for (int64_t m = r; m < M; m += 8) a += dZ[m * N + j];
+    sh[r][threadIdx.x & 31] = a;
+    __syncthreads();
+    if (r == 0 && j < N) {
+        float s = 0.f;
+        for (int q = 0; q < 8; ++q) s += sh[q][threadIdx.x & 31];
+        out[j] = s;
+    }
+}
+
+__global__ void to_bf16_kernel(const float *x, int64_t n, __nv_bfloat16 *y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+__global__ void adamw_kernel(int64_t n, float *w, const float *g, float *m, float *v, float lr, float b1, float b2,
+                             float eps, float wd, float c1, float c2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * w[i]);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+struct MlpLayout {
+    int64_t oW1, ob1, oW2, ob2, oW3, ob3, n;
+};
+
+static MlpLayout mlp_layout(const fhr_mlp_dims *d) {
+    MlpLayout L;
+    L.oW1 = 0;
+    L.ob1 = L.oW1 + (int64_t)d->H1 * d->Nk;
+    L.oW2 = L.ob1 + d->H1;
+    L.ob2 = L.oW2 + (int64_t)d->H2 * d->H1;
+    L.oW3 = L.ob2 + d->H2;
+    L.ob3 = L.oW3 + (int64_t)d->K * d->H2;
+    L.n = L.ob3 + d->K;
+    return L;
+}
+
+constexpr int kMlpChunk = 32768;      // pixel rows per forward/backward chunk
+constexpr int kSplitRows = 2048;      // contraction rows per split of a weight gradient
+
+struct MlpWs {
+    int *status;
+    __nv_bfloat16 *wb;      // bf16 weights (packed like the params) or null
+    float *Z1, *Z2, *Z3, *Y;
+    void *A1, *A2;
+    float *dZ3, *dZ2, *dZ1;
+    float *part;            // split-K partials
+    double *lpart;
+    double *lacc;
+};
+
+static int64_t mlp_splits(int64_t M) { return cdiv(M, kSplitRows); }
+
+static size_t carve_mlp(void *base, const fhr_mlp_dims *d, int train, MlpWs *w) {
+    const MlpLayout L = mlp_layout(d);
+    const int64_t R = kMlpChunk;
+    const int es = d->weights_bf16 ? 2 : 4;
+    Carve c(base);
+    MlpWs t{};
+    t.status = c.take<int>(kStatusBytes / sizeof(int));
+    t.wb = d->weights_bf16 ? c.take<__nv_bfloat16>((size_t)L.n) : nullptr;
+    t.Z1 = c.take<float>((size_t)R * d->H1);
+    t.Z2 = c.take<float>((size_t)R * d->H2);
+    t.Z3 = c.take<float>((size_t)R * d->K);
+    t.Y = c.take<float>((size_t)R * d->K);
+    t.A1 = c.take<char>((size_t)R * d->H1 * es);
+    t.A2 = c.take<char>((size_t)R * d->H2 * es);
+    if (train) {
+        t.dZ3 = c.take<float>((size_t)R * d->K);
+        t.dZ2 = c.take<float>((size_t)R * d->H2);
+        t.dZ1 = c.take<float>((size_t)R * d->H1);
+        const int64_t big = std::max<int64_t>((int64_t)d->H1 * d->Nk, (int64_t)d->H2 * d->H1);
+        t.part = c.take<float>((size_t)mlp_splits(R) * big);
+        t.lpart = c.take<double>(1024);
+        t.lacc = c.take<double>(1);
+    }
+    if (w) *w = t;
+    return c.size();
+}
+
+static fhr_status check_dims(fhr_ctx *ctx, const fhr_mlp_dims *d) {
+    FHR_ARG(d, "dims is null");
+    FHR_ARG(d->Nk > 0 && d->H1 > 0 && d->H2 > 0 && d->K >= 1 && d->K <= 64, "bad MLP dimensions");
+    FHR_ARG(d->ldx >= d->Nk, "ldx < Nk");
+    FHR_ARG(d->x_dtype == FHR_F32 || d->x_dtype == FHR_BF16, "bad x_dtype");
+    return FHR_OK;
+}
+
+template <typename TA, typename TB, int EPI>
+static fhr_status gemm(fhr_ctx *ctx, const GemmArgs &g, int splits = 1) {
+    dim3 grid((unsigned)cdiv(g.N, GBN), (unsigned)cdiv(g.M, GBM), (unsigned)splits);
+    gemm_kernel<TA, TB, EPI><<<grid, 256, 0, ctx->stream>>>(g);
+    FHR_LAUNCHED();
+    return FHR_OK;
+}
+
+// weights as seen by the GEMMs: bf16 copies or the f32 master
+template <typename TW>
+static const void *wptr(const float *prm, const MlpWs &w, int64_t off) {
+    if (sizeof(TW) == 2) return w.wb + off;
+    return prm + off;
+}
+
+// forward of `rows` pixel rows starting at X (row stride ldx); fills Z1..Y
+template <typename TX, typename TW>
+static fhr_status forward_chunk(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *prm, const MlpWs &w, int64_t rows,
+                                const void *X, float *Yout, float *Z3out) {
+    const MlpLayout L = mlp_layout(d);
+    GemmArgs g{};
+    // layer 1: Z1 = X W1^T + b1
+    g.M = (int)rows; g.N = d->H1; g.Kd = d->Nk;
+    g.A = X; g.sai = d->ldx; g.sak = 1;
+    g.B = wptr<TW>(prm, w, L.oW1); g.sbk = 1; g.sbj = d->Nk;
+    g.C = w.Z1; g.ldc = d->H1;
+    g.C2 = w.A1; g.c2_bf16 = sizeof(TW) == 2; g.ldc2 = d->H1;
+    g.bias = prm + L.ob1; g.kchunk = g.Kd;
+    FHR_TRY((gemm<TX, TW, EPI_BIAS_GELU>(ctx, g)));
+    // layer 2
+    g.N = d->H2; g.Kd = d->H1;
+    g.A = w.A1; g.sai = d->H1;
+    g.B = wptr<TW>(prm, w, L.oW2); g.sbj = d->H1;
+    g.C = w.Z2; g.ldc = d->H2; g.C2 = w.A2; g.ldc2 = d->H2;
+    g.bias = prm + L.ob2; g.kchunk = g.Kd;
+    FHR_TRY((gemm<TW, TW, EPI_BIAS_GELU>(ctx, g)));
+    // layer 3: Y = softplus(A2 W3^T + b3)
+    g.N = d->K; g.Kd = d->H2;
+    g.A = w.A2; g.sai = d->H2;
+    g.B = wptr<TW>(prm, w, L.oW3); g.sbj = d->H2;
+    g.C = Yout; g.ldc = d->K; g.C2 = Z3out; g.ldc2 = d->K;
+    g.bias = prm + L.ob3; g.kchunk = g.Kd;
+    FHR_TRY((gemm<TW, TW, EPI_BIAS_SOFTPLUS>(ctx, g)));
+    return FHR_OK;
+}
+
+// backward of a chunk: accumulates parameter gradients into grad (+=)
+template <typename TX, typename TW>
+static fhr_status backward_chunk(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *prm, const MlpWs &w, int64_t rows,
+                                 const void *X, float *grad) {
+    const MlpLayout L = mlp_layout(d);
+    const int splits = (int)mlp_splits(rows);
+    auto wgrad = [&](const float *dZ, int nout, const void *act, int nin, int act_bf16, int64_t off) -> fhr_status {
+        // grad[off + o*nin + i] += sum_m dZ[m][o] act[m][i]
+        GemmArgs g{};
+        g.M = nout; g.N = nin; g.Kd = (int)rows;
+        g.A = dZ; g.sai = 1; g.sak = nout;
+        g.B = act; g.sbk = nin; g.sbj = 1;
+        g.C = w.part; g.ldc = nin; g.split_stride = (int64_t)nout * nin; g.kchunk = kSplitRows;
+        if (act_bf16) FHR_TRY((gemm<float, __nv_bfloat16, EPI_STORE>(ctx, g, splits)));
+        else FHR_TRY((gemm<float, float, EPI_STORE>(ctx, g, splits)));
+        const int64_t n = (int64_t)nout * nin;
+        mlp_reduce_splits<<<(unsigned)std::min<int64_t>(cdiv(n, 256), 4096), 256, 0, ctx->stream>>>(w.part, splits, n,
+                                                                                                    grad + off);
+        FHR_LAUNCHED();
+        return FHR_OK;
+    };
+    auto bgrad = [&](const float *dZ, int n, float *out) -> fhr_status {
+        mlp_colsum<<<(unsigned)cdiv(n, 32), 256, 0, ctx->stream>>>(dZ, rows, n, out);
+        FHR_LAUNCHED();
+        return FHR_OK;
+    };
+    const int wb = sizeof(TW) == 2;
+    // layer 3
+    FHR_TRY(wgrad(w.dZ3, d->K, w.A2, d->H2, wb, L.oW3));
+    FHR_TRY(bgrad(w.dZ3, d->K, grad + L.ob3));
+    // dZ2 = (dZ3 W3) * gelu'(Z2)
+    {
+        GemmArgs g{};
+        g.M = (int)rows; g.N = d->H2; g.Kd = d->K;
+        g.A = w.dZ3; g.sai = d->K; g.sak = 1;
+        g.B = wptr<TW>(prm, w, L.oW3); g.sbk = d->H2; g.sbj = 1;
+        g.C = w.dZ2; g.ldc = d->H2; g.Z = w.Z2; g.ldz = d->H2; g.kchunk = g.Kd;
+        FHR_TRY((gemm<float, TW, EPI_GELU_BACK>(ctx, g)));
+    }
+    FHR_TRY(wgrad(w.dZ2, d->H2, w.A1, d->H1, wb, L.oW2));
+    FHR_TRY(bgrad(w.dZ2, d->H2, grad + L.ob2));
+    // dZ1 = (dZ2 W2) * gelu'(Z1)
+    {
+        GemmArgs g{};
+        g.M = (int)rows; g.N = d->H1; g.Kd = d->H2;
+        g.A = w.dZ2; g.sai = d->H2; g.sak = 1;
+        g.B = wptr<TW>(prm, w, L.oW2); g.sbk = d->H1; g.sbj = 1;
+        g.C = w.dZ1; g.ldc = d->H1; g.Z = w.Z1; g.ldz = d->H1; g.kchunk = g.Kd;
+        FHR_TRY((gemm<float, TW, EPI_GELU_BACK>(ctx, g)));
+    }
+    // layer 1 weights against the input rows (row stride ldx)
+    {
+        GemmArgs g{};
+        g.M = d->H1; g.N = d->Nk; g.Kd = (int)rows;
+        g.A = w.dZ1; g.sai = 1; g.sak = d->H1;
+        g.B = X; g.sbk = d->ldx; g.sbj = 1;
+        g.C = w.part; g.ldc = d->Nk; g.split_stride = (int64_t)d->H1 * d->Nk; g.kchunk = kSplitRows;
+        FHR_TRY((gemm<float, TX, EPI_STORE>(ctx, g, splits)));
+        const int64_t n = (int64_t)d->H1 * d->Nk;
+        mlp_reduce_splits<<<(unsigned)std::min<int64_t>(cdiv(n, 256), 4096), 256, 0, ctx->stream>>>(
+            w.part, splits, n, grad + L.oW1);
+        FHR_LAUNCHED();
+    }
+    FHR_TRY(bgrad(w.dZ1, d->H1, grad + L.ob1));
+    return FHR_OK;
+}
+
+static fhr_status prep_weights(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *prm, const MlpWs &w) {
+    if (!d->weights_bf16) return FHR_OK;
+    const MlpLayout L = mlp_layout(d);
+    to_bf16_kernel<<<(unsigned)std::min<int64_t>(cdiv(L.n, 256), 4096), 256, 0, ctx->stream>>>(prm, L.n, w.wb);
+    FHR_LAUNCHED();
+    return FHR_OK;
+}
+
+template <typename TX, typename TW>
+static fhr_status forward_all(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *prm, const MlpWs &w, int64_t M,
+                              const void *X, float *Y) {
+    const int es = d->x_dtype == FHR_BF16 ? 2 : 4;
+    for (int64_t r0 = 0; r0 < M; r0 += kMlpChunk) {
+        const int64_t rows = std::min<int64_t>(kMlpChunk, M - r0);
+        FHR_TRY((forward_chunk<TX, TW>(ctx, d, prm, w, rows, (const char *)X + r0 * d->ldx * es, Y + r0 * d->K,
+                                       w.Z3)));
+    }
+    return FHR_OK;
+}
+
+fhr_status mlp_forward_impl(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *prm, int64_t M, const void *X, float *Y,
+                            void *ws, size_t ws_bytes) {
+    FHR_TRY(check_dims(ctx, d));
+    FHR_ARG(prm && X && Y && ws, "null pointer argument");
+    FHR_ARG(M >= 0, "M < 0");
+    MlpWs w;
+    const size_t need = carve_mlp(ws, d, 0, &w);
+    FHR_ARG(ws_bytes >= need, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+    FHR_CUDA(cudaSetDevice(ctx->device));
+    FHR_TRY(prep_weights(ctx, d, prm, w));
+    if (d->x_dtype == FHR_BF16) {
+        if (d->weights_bf16) return forward_all<__nv_bfloat16, __nv_bfloat16>(ctx, d, prm, w, M, X, Y);
+        return forward_all<__nv_bfloat16, float>(ctx, d, prm, w, M, X, Y);
+    }
+    if (d->weights_bf16) return forward_all<float, __nv_bfloat16>(ctx, d, prm, w, M, X, Y);
+    return forward_all<float, float>(ctx, d, prm, w, M, X, Y);
+}
+
+size_t mlp_ws_bytes(const fhr_mlp_dims *d, int train) { return carve_mlp(nullptr, d, train, nullptr); }
+
+template <typename TX, typename TW>
+static fhr_status grad_impl(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *prm, const MlpWs &w, int64_t M,
+                            const void *X, const float *T, float *grad, double *loss) {
+    FHR_ARG(M > 0 && M <= kMlpChunk, "fhr_mlp_grad takes 1..%d rows per call", kMlpChunk);
+    FHR_TRY((forward_chunk<TX, TW>(ctx, d, prm, w, M, X, w.Y, w.Z3)));
+    const int64_t n = M * d->K;
+    const int nb = (int)std::min<int64_t>(cdiv(n, 256), 1024);
+    mlp_loss_kernel<<<nb, 256, 0, ctx->stream>>>(w.Y, w.Z3, T, n, 2.f / (float)n, w.dZ3, w.lpart);
+    FHR_LAUNCHED();
+    mlp_loss_final<<<1, 32, 0, ctx->stream>>>(w.lpart, nb, 1.0 / (double)n, loss ? loss : w.lacc);
+    FHR_LAUNCHED();
+    return backward_chunk<TX, TW>(ctx, d, prm, w, M, X, grad);
+}
+
+}  // namespace fhr
+
+using namespace fhr;
+
+extern "C" fhr_status fhr_mlp_workspace_size(fhr_ctx *ctx, const fhr_mlp_dims *d, int train, size_t *bytes) {
+    if (!ctx) return FHR_ERR_ARG;
+    FHR_TRY(check_dims(ctx, d));
+    FHR_ARG(bytes, "bytes is null");
+    *bytes = carve_mlp(nullptr, d, train, nullptr);
+    return FHR_OK;
+}
+
+extern "C" fhr_status fhr_mlp_forward(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *params, int64_t M,
+                                      const void *X, float *Y, void *ws, size_t ws_bytes) {
+    if (!ctx) return FHR_ERR_ARG;
+    return mlp_forward_impl(ctx, d, params, M, X, Y, ws, ws_bytes);
+}
+
+extern "C" fhr_status fhr_mlp_grad(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *params, int64_t M, const void *X,
+                                   const float *T, float *grad, double *loss, void *ws, size_t ws_bytes) {
+    if (!ctx) return FHR_ERR_ARG;
+    FHR_TRY(check_dims(ctx, d));
+    FHR_ARG(params && X && T && grad && ws, "null pointer argument");
+    MlpWs w;
+    const size_t need = carve_mlp(ws, d, 1, &w);
+    FHR_ARG(ws_bytes >= need, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+    FHR_CUDA(cudaSetDevice(ctx->device));
+    FHR_TRY(prep_weights(ctx, d, params, w));
+    if (d->x_dtype == FHR_BF16) {
+        if (d->weights_bf16) return grad_impl<__nv_bfloat16, __nv_bfloat16>(ctx, d, params, w, M, X, T, grad, loss);
+        return grad_impl<__nv_bfloat16, float>(ctx, d, params, w, M, X, T, grad, loss);
+    }
+    if (d->weights_bf16) return grad_impl<float, __nv_bfloat16>(ctx, d, params, w, M, X, T, grad, loss);
+    return grad_impl<float, float>(ctx, d, params, w, M, X, T, grad, loss);
+}
+
+extern "C" fhr_status fhr_mlp_adamw(fhr_ctx *ctx, int64_t n, float *params, const float *grad, float *m, float *v,
+                                    int step, float lr, float beta1, float beta2, float eps, float weight_decay) {
+    if (!ctx) return FHR_ERR_ARG;
+    FHR_ARG(params && grad && m && v && n > 0 && step >= 1, "bad AdamW arguments");
+    FHR_CUDA(cudaSetDevice(ctx->device));
+    const float c1 = (float)(1.0 - pow((double)beta1, step)), c2 = (float)(1.0 - pow((double)beta2, step));
+    adamw_kernel<<<(unsigned)std::min<int64_t>(cdiv(n, 256), 4096), 256, 0, ctx->stream>>>(
+        n, params, grad, m, v, lr, beta1, beta2, eps, weight_decay, c1, c2);
+    FHR_LAUNCHED();
+    return FHR_OK;
+}

@@ -221,6 +221,28 @@ __global__ void nmf_update_d(const double *Q64, const double *GW64, const double
     }
 }
 
+// Learned start: D0 from `sweeps` HALS D half-steps from D = 0 with Q = P^T W0
+// and G_W = W0^T W0 fixed (no further passes over P).  One thread per bin.
+__global__ void nmf_d_from_q(const double *Q64, const double *GW64, int Nk, int K, int sweeps, float *D) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nk) return;
+    double d[kMaxK], q[kMaxK], gw[kMaxK * kMaxK];
+    for (int s = 0; s < K; ++s) {
+        d[s] = 0.0;
+        q[s] = Q64[(size_t)k * K + s];
+    }
+    for (int i = 0; i < K * K; ++i) gw[i] = GW64[i];
+    for (int it = 0; it < sweeps; ++it)
+        for (int s = 0; s < K; ++s) {
+            const double h = gw[s * K + s];
+            if (h == 0.0) continue;
+            double g = q[s];
+            for (int t = 0; t < K; ++t) g -= d[t] * gw[t * K + s];
+            d[s] = fmax(0.0, d[s] + g / h);
+        }
+    for (int s = 0; s < K; ++s) D[(size_t)k * K + s] = (float)d[s];
+}
+
 // Final outputs: D = D64 * invn, W *= wscale.
 __global__ void nmf_finalize(const double *D64, const NmfState *st, int Nk, int K, float *D, float *W, int64_t Np) {
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -239,12 +261,20 @@ static fhr_status check_nmf(fhr_ctx *ctx, const fhr_nmf_params *p) {
     FHR_ARG(p->ldP % (p->p_dtype == FHR_BF16 ? 8 : 4) == 0, "ldP must be a multiple of 16 bytes");
     FHR_ARG(p->iters >= 0, "iters < 0");
     FHR_ARG(p->K <= p->Nk && (int64_t)p->K <= p->Np, "K > min(Nk, Np)");
-    if (p->init != FHR_INIT_GIVEN && p->init != FHR_INIT_NNDSVD)
+    if (p->init != FHR_INIT_GIVEN && p->init != FHR_INIT_NNDSVD && p->init != FHR_INIT_LEARNED)
         return set_error(ctx, FHR_ERR_ARG, "unknown init %d", p->init);
+    if (p->init == FHR_INIT_LEARNED) {
+        FHR_ARG(p->mlp && p->mlp_params, "FHR_INIT_LEARNED needs mlp and mlp_params");
+        FHR_ARG(p->mlp->K == p->K && p->mlp->Nk == p->Nk && p->mlp->ldx == p->ldP && p->mlp->x_dtype == p->p_dtype,
+                "the warm-start network does not match the problem (K, Nk, ldP, p_dtype)");
+    }
     return FHR_OK;
 }
 
 fhr_status nndsvd_ws_size(fhr_ctx *ctx, const fhr_nmf_params *p, size_t *bytes);
+size_t mlp_ws_bytes(const fhr_mlp_dims *d, int train);
+fhr_status mlp_forward_impl(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *prm, int64_t M, const void *X, float *Y,
+                            void *ws, size_t ws_bytes);
 fhr_status nndsvd_run(fhr_ctx *ctx, const fhr_nmf_params *p, const void *P, float *D, float *W, void *region,
                       int *status);
 
@@ -255,6 +285,7 @@ static fhr_status decompose_ws(fhr_ctx *ctx, const fhr_nmf_params *p, const Pass
     size_t a = carve_nmf(base, p->Np, p->Nk, p->K, cfg.grid, p->iters, w);
     size_t b = 0;
     if (p->init == FHR_INIT_NNDSVD) FHR_TRY(nndsvd_ws_size(ctx, p, &b));
+    if (p->init == FHR_INIT_LEARNED) b = mlp_ws_bytes(p->mlp, 0);
     if (nn_region) *nn_region = base ? (void *)((char *)base + a) : nullptr;
     *total = a + b;
     return FHR_OK;
@@ -295,10 +326,25 @@ extern "C" fhr_status fhr_decompose(fhr_ctx *ctx, const fhr_nmf_params *p, const
     const int K = p->K, Nk = p->Nk;
 
     if (p->init == FHR_INIT_NNDSVD) FHR_TRY(nndsvd_run(ctx, p, P, D, W, nn_region, w.status));
+    PassArgs a;
+    if (p->init == FHR_INIT_LEARNED) {
+        FHR_TRY(mlp_forward_impl(ctx, p->mlp, p->mlp_params, p->Np, P, W, nn_region, mlp_ws_bytes(p->mlp, 0)));
+        // unit state, then one pass with W0 fixed for Q = P^T W0, G_W = W0^T W0
+        nmf_init_given<<<1, 256, 0, st>>>(D, Nk, K, w.D64, &w.state[0]);
+        FHR_LAUNCHED();
+        a.P = P; a.Np = p->Np; a.Nk = Nk; a.ldP = p->ldP; a.D64 = w.D64; a.st = &w.state[0]; a.W = W;
+        a.Qpart = w.Qpart; a.Gpart = w.Gpart; a.ssqpart = w.ssqpart; a.status = w.status;
+        a.mode = PASS_GIVEN_W; a.want_ssq = 0;
+        FHR_TRY(launch_pass(ctx, cfg, a));
+        nmf_reduce<<<(unsigned)cdiv(Nk * K, 32) + 1, 256, 0, st>>>(w.Qpart, w.Gpart, w.ssqpart, cfg.grid, Nk * K, K,
+                                                                    w.Q64, w.GW64, w.ssq64, 0);
+        FHR_LAUNCHED();
+        nmf_d_from_q<<<(unsigned)cdiv(Nk, 128), 128, 0, st>>>(w.Q64, w.GW64, Nk, K, 10, D);
+        FHR_LAUNCHED();
+    }
     nmf_init_given<<<1, 256, 0, st>>>(D, Nk, K, w.D64, &w.state[0]);
     FHR_LAUNCHED();
 
-    PassArgs a;
     a.P = P;
     a.Np = p->Np;
     a.Nk = Nk;

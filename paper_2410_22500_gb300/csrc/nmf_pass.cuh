@@ -28,7 +28,7 @@ namespace fhr {
 constexpr int kPassRows = 4;       // pixel rows per tile
 constexpr int kMaxK = 8;
 
-enum PassMode { PASS_HALS = 0, PASS_PROJECT = 1, PASS_PROJECT_STORE = 2 };
+enum PassMode { PASS_HALS = 0, PASS_PROJECT = 1, PASS_PROJECT_STORE = 2, PASS_GIVEN_W = 3 };
 
 // Iteration state published by the D-update kernel for the next pass.
 struct NmfState {
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256, (PassOcc<K, CPT, TP>::MINB)) nmf_pass_ker
         float wold[K], wnext[K];
         auto fetch = [&](int64_t i, float *dst) {
             const int64_t r0 = (blockIdx.x + i * gridDim.x) * ROWS;
-            if (a.mode == PASS_HALS && i < my_tiles && r0 + lane < a.Np && lane < ROWS) {
+            if ((a.mode == PASS_HALS || a.mode == PASS_GIVEN_W) && i < my_tiles && r0 + lane < a.Np && lane < ROWS) {
 #pragma unroll
                 for (int s = 0; s < K; ++s) dst[s] = a.W[(r0 + lane) * K + s];
             }
@@ -368,6 +368,10 @@ __global__ void __launch_bounds__(256, (PassOcc<K, CPT, TP>::MINB)) nmf_pass_ker
                     }
 #pragma unroll
                     for (int s = 0; s < K; ++s) a.W[(r0 + lane) * K + s] = w[s];
+                } else if (a.mode == PASS_GIVEN_W) {
+                    // W held fixed: only P^T W and W^T W are accumulated
+#pragma unroll
+                    for (int s = 0; s < K; ++s) w[s] = wold[s] * wsc[s];
                 } else {
 #pragma unroll
                     for (int s = 0; s < K; ++s) w[s] = r[s];

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfhr.so")
 
 F32, BF16 = 0, 1
-INIT_GIVEN, INIT_NNDSVD = 0, 1
+INIT_GIVEN, INIT_NNDSVD, INIT_LEARNED = 0, 1, 2
 OK, ERR_ARG, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 
 # Every entry point declared in include/fhr.h (checked by the ABI test).
@@ -23,7 +23,7 @@ ENTRY_POINTS = (
     "fhr_normalise", "fhr_decompose_workspace_size", "fhr_decompose", "fhr_projector_workspace_size",
     "fhr_project", "fhr_backproject", "fhr_reconstruct_workspace_size", "fhr_reconstruct", "fhr_expand",
     "fhr_pipeline_workspace_size", "fhr_pipeline", "fhr_profile_enable", "fhr_profile_read",
-    "fhr_decompose_static",
+    "fhr_decompose_static", "fhr_mlp_workspace_size", "fhr_mlp_forward", "fhr_mlp_grad", "fhr_mlp_adamw",
 )
 
 
@@ -35,7 +35,8 @@ class NormParams(ctypes.Structure):
 class NmfParams(ctypes.Structure):
     _fields_ = [("Np", ctypes.c_int64), ("Nk", ctypes.c_int), ("ldP", ctypes.c_int), ("K", ctypes.c_int),
                 ("iters", ctypes.c_int), ("init", ctypes.c_int), ("p_dtype", ctypes.c_int),
-                ("power_iters", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("power_iters", ctypes.c_int), ("seed", ctypes.c_uint64), ("mlp", ctypes.c_void_p),
+                ("mlp_params", ctypes.c_void_p)]
 
 
 class Geom(ctypes.Structure):
@@ -48,6 +49,15 @@ class MbirParams(ctypes.Structure):
                 ("T", ctypes.c_float), ("beta", ctypes.c_float), ("snr_db", ctypes.c_float),
                 ("momentum", ctypes.c_int), ("sigma_v", ctypes.POINTER(ctypes.c_float)),
                 ("sigma_x", ctypes.POINTER(ctypes.c_float))]
+
+
+class MlpDims(ctypes.Structure):
+    _fields_ = [("Nk", ctypes.c_int), ("H1", ctypes.c_int), ("H2", ctypes.c_int), ("K", ctypes.c_int),
+                ("ldx", ctypes.c_int), ("x_dtype", ctypes.c_int), ("weights_bf16", ctypes.c_int)]
+
+
+def mlp_nparams(Nk, H1, H2, K):
+    return H1 * Nk + H1 + H2 * H1 + H2 + K * H2 + K
 
 
 class PipelineParams(ctypes.Structure):
@@ -92,6 +102,10 @@ def load():
         L.fhr_pipeline_workspace_size.argtypes = [vp, ctypes.POINTER(PipelineParams), szp]
         L.fhr_pipeline.argtypes = [vp, ctypes.POINTER(PipelineParams), vp, vp, vp, vp, vp, vp, vp, vp, sz]
         L.fhr_decompose_static.argtypes = [vp, ctypes.POINTER(NmfParams), vp, vp, vp, vp]
+        L.fhr_mlp_workspace_size.argtypes = [vp, ctypes.POINTER(MlpDims), ctypes.c_int, szp]
+        L.fhr_mlp_forward.argtypes = [vp, ctypes.POINTER(MlpDims), vp, ctypes.c_int64, vp, vp, vp, sz]
+        L.fhr_mlp_grad.argtypes = [vp, ctypes.POINTER(MlpDims), vp, ctypes.c_int64, vp, vp, vp, vp, vp, sz]
+        L.fhr_mlp_adamw.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.c_int] + [ctypes.c_float] * 5
         L.fhr_profile_enable.argtypes = [vp, ctypes.c_int]
         L.fhr_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_double)]
@@ -185,13 +199,19 @@ class Context:
         return (P, b) if bg is not None else P
 
     # ------------------------------------------------------------ decompose
-    def nmf_params(self, P, Nk, K, iters, init=INIT_GIVEN, power_iters=0, seed=0):
+    def nmf_params(self, P, Nk, K, iters, init=INIT_GIVEN, power_iters=0, seed=0, mlp=None):
         torch = _torch()
-        return NmfParams(P.shape[0], Nk, P.shape[1], K, iters, init,
-                         BF16 if P.dtype == torch.bfloat16 else F32, power_iters, seed)
+        prm = NmfParams(P.shape[0], Nk, P.shape[1], K, iters, init,
+                        BF16 if P.dtype == torch.bfloat16 else F32, power_iters, seed)
+        if mlp is not None:
+            dims, params = mlp
+            prm.mlp = ctypes.addressof(dims)
+            prm.mlp_params = params.data_ptr()
+            prm._keep = (dims, params)
+        return prm
 
     def decompose(self, P, Nk, K, iters, *, D=None, W=None, init=None, power_iters=0, seed=0, obj=True,
-                  check_status=True):
+                  check_status=True, mlp=None):
         """Fast-HALS NMF of P (Sec. III).  D [Nk][K], W [Np][K] updated in place (GIVEN) or filled (NNDSVD)."""
         torch = _torch()
         dev = P.device
@@ -201,7 +221,9 @@ class Context:
             D = torch.zeros((Nk, K), dtype=torch.float32, device=dev)
         if W is None:
             W = torch.zeros((P.shape[0], K), dtype=torch.float32, device=dev)
-        prm = self.nmf_params(P, Nk, K, iters, init, power_iters, seed)
+        if mlp is not None:
+            init = INIT_LEARNED
+        prm = self.nmf_params(P, Nk, K, iters, init, power_iters, seed, mlp)
         n = ctypes.c_size_t()
         self.check(self.L.fhr_decompose_workspace_size(self._h, ctypes.byref(prm), ctypes.byref(n)))
         ws = self.workspace(n.value)
@@ -289,6 +311,44 @@ class Context:
         self.check(self.L.fhr_expand(self._h, N, Nr, K, Nk, k0, k1, _ptr(xs), _ptr(D), xh_dtype, _ptr(xh)))
         return xh
 
+    # ------------------------------------------------------------ learned warm start (MLP)
+    @staticmethod
+    def mlp_dims(Nk, H1, H2, K, *, ldx=None, x_bf16=False, weights_bf16=False):
+        return MlpDims(Nk, H1, H2, K, ldx or Nk, BF16 if x_bf16 else F32, int(weights_bf16))
+
+    def mlp_forward(self, dims, params, X, *, Y=None, ws=None):
+        """Y [M][K] = MLP(X), X [M][ldx] (f32 or bf16), params packed f32."""
+        torch = _torch()
+        M = X.shape[0]
+        if ws is None:
+            n = ctypes.c_size_t()
+            self.check(self.L.fhr_mlp_workspace_size(self._h, ctypes.byref(dims), 0, ctypes.byref(n)))
+            ws = self.workspace(n.value)
+        if Y is None:
+            Y = torch.empty((M, dims.K), dtype=torch.float32, device=X.device)
+        self.check(self.L.fhr_mlp_forward(self._h, ctypes.byref(dims), _ptr(params), M, _ptr(X), _ptr(Y), _ptr(ws),
+                                          ws.numel()))
+        return Y
+
+    def mlp_grad(self, dims, params, X, T, *, grad=None, loss=None, ws=None):
+        """(loss, grad) of the mean-squared error of MLP(X) against T; up to 32768 rows."""
+        torch = _torch()
+        if ws is None:
+            n = ctypes.c_size_t()
+            self.check(self.L.fhr_mlp_workspace_size(self._h, ctypes.byref(dims), 1, ctypes.byref(n)))
+            ws = self.workspace(n.value)
+        if grad is None:
+            grad = torch.empty_like(params)
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float64, device=X.device)
+        self.check(self.L.fhr_mlp_grad(self._h, ctypes.byref(dims), _ptr(params), X.shape[0], _ptr(X), _ptr(T),
+                                       _ptr(grad), _ptr(loss), _ptr(ws), ws.numel()))
+        return loss, grad
+
+    def mlp_adamw(self, params, grad, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, wd=1e-4):
+        self.check(self.L.fhr_mlp_adamw(self._h, params.numel(), _ptr(params), _ptr(grad), _ptr(m), _ptr(v), step,
+                                        lr, b1, b2, eps, wd))
+
     # ------------------------------------------------------------ pipeline
     def pipeline_params(self, *, Nv, Nr, Nc, Nk, N, K, nmf_iters, mbir_iters, p_dtype=F32, xh_dtype=F32,
                         host_io=False, power_iters=0, seed=0, angles=None, **mbir_kw):
@@ -296,7 +356,7 @@ class Context:
         ldP = (Nk + mult - 1) // mult * mult
         prm = PipelineParams()
         prm.norm = NormParams(Nv, Nr, Nc, Nk, ldP, p_dtype)
-        prm.nmf = NmfParams(Nv * Nr * Nc, Nk, ldP, K, nmf_iters, INIT_NNDSVD, p_dtype, power_iters, seed)
+        prm.nmf = NmfParams(Nv * Nr * Nc, Nk, ldP, K, nmf_iters, INIT_NNDSVD, p_dtype, power_iters, seed, None, None)
         prm.geom = self.geom(N, Nr, Nc, Nv, angles)
         mp = self.mbir_params(K, mbir_iters, **mbir_kw)
         prm.mbir = mp

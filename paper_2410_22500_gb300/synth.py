@@ -234,16 +234,17 @@ def volume_fractions(ph: Phantom, N: int, Nr: int, sub: int = 4) -> np.ndarray:
 
 def make_problem(*, N: int, Nr: int, Nc: int, Nv: int, Nk: int, Nm: int, I0: float,
                  seed: int, dead_frac: float = 0.0, peak_integral: float = 2.0,
-                 three_d: bool | None = None) -> Problem:
+                 three_d: bool | None = None, spectra: np.ndarray | None = None) -> Problem:
     """Draw phantom, spectra and dead-bin mask; scale spectra so the largest
-    noise-free line integral over all pixels and bins is about `peak_integral`."""
+    noise-free line integral over all pixels and bins is about `peak_integral`.
+    `spectra` [Nk][Nm] fixes the materials' spectral shapes (a shared library)."""
     rng = np.random.default_rng(seed)
     g = Geometry(N=N, Nr=Nr, Nc=Nc, Nv=Nv)
     if three_d is None:
         three_d = Nr > 1
     ph = ellipsoid_phantom(rng, N, Nr, Nm) if three_d else disk_phantom(rng, N, Nm)
     lam = wavelengths(Nk)
-    mu = material_spectra(rng, Nm, lam)
+    mu = material_spectra(rng, Nm, lam) if spectra is None else np.array(spectra, dtype=np.float64, copy=True)
     C = chords(ph, g).reshape(-1, Nm)
     bound = float((C * mu.max(axis=0)[None, :]).sum(axis=1).max())
     mu *= peak_integral / max(bound, 1e-30)
@@ -359,6 +360,11 @@ def scaled(pb_fn, **over) -> Problem:
               dead_frac=float(base.dead_bins.mean()))
     kw.update(over)
     return make_problem(**kw)
+
+
+def spectra_library(Nk: int, Nm: int, seed: int = 77) -> np.ndarray:
+    """One fixed set of Nm material spectra [Nk][Nm] shared by a family of phantoms."""
+    return material_spectra(np.random.default_rng(seed), Nm, wavelengths(Nk))
 
 
 def random_counts(rng: np.random.Generator, shape, lo=0, hi=2000) -> np.ndarray:

@@ -56,9 +56,9 @@ def test_struct_layout_matches_c(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(fhr_norm_params), sizeof(fhr_nmf_params), sizeof(fhr_geom),
          sizeof(fhr_mbir_params), sizeof(fhr_pipeline_params));
-  printf("%zu %zu %zu %zu %zu\n", offsetof(fhr_nmf_params, seed), offsetof(fhr_mbir_params, sigma_v),
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", offsetof(fhr_nmf_params, seed), offsetof(fhr_mbir_params, sigma_v),
          offsetof(fhr_pipeline_params, geom), offsetof(fhr_pipeline_params, mbir),
-         offsetof(fhr_pipeline_params, host_io));
+         offsetof(fhr_pipeline_params, host_io), offsetof(fhr_nmf_params, mlp_params), sizeof(fhr_mlp_dims));
   return 0;
 }
 ''')
@@ -68,7 +68,8 @@ int main(void) {
     assert sizes == [ctypes.sizeof(t) for t in (fhr.NormParams, fhr.NmfParams, fhr.Geom, fhr.MbirParams,
                                                  fhr.PipelineParams)]
     assert offs == [fhr.NmfParams.seed.offset, fhr.MbirParams.sigma_v.offset, fhr.PipelineParams.geom.offset,
-                    fhr.PipelineParams.mbir.offset, fhr.PipelineParams.host_io.offset]
+                    fhr.PipelineParams.mbir.offset, fhr.PipelineParams.host_io.offset, fhr.NmfParams.mlp_params.offset,
+                    ctypes.sizeof(fhr.MlpDims)]
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
