@@ -231,6 +231,44 @@ fhr_status fhr_reconstruct(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_param
                            const float *sino, float *xs, void *ws, size_t ws_bytes);
 
 /* ------------------------------------------------------------------------
+ * Batched MBIR: Eq. (recon) for every channel and slice of nprob independent
+ * problems of uneven size in ONE persistent cooperative launch (replayed from
+ * a CUDA graph), two grid-wide phases per iteration (forward residual; fused
+ * backward gather + SQS update) separated by bounded grid barriers.
+ * probs is a HOST array; each problem's sinogram/volume are device pointers
+ * with the layouts of fhr_reconstruct (Wl = Nr*K <= 256); sigma_v[0] > 0 and
+ * sigma_x[0] > 0 select explicit per-channel sigmas, else the defaults of
+ * fhr_reconstruct.  All problems share the prior parameters and iteration
+ * count, and must all be 2-D (Nr = 1) or all 3-D.
+ * tile: rays / pixels per work item in block-wide sweeps (0 = 2);
+ * fhr_reconstruct_batch_autotune times the candidates {1,2,4,8,16} on the
+ * batch (xs is not modified) and returns the fastest.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int N, Nr, Nc, Nv, K;
+    const double *angles;
+    const float *sino;
+    float *xs;
+    float sigma_v[8], sigma_x[8];
+} fhr_problem;
+
+typedef struct {
+    int iters;
+    float p, q, T, beta;
+    float snr_db;
+    int momentum;
+    int tile;
+} fhr_batch_params;
+
+fhr_status fhr_reconstruct_batch_workspace_size(fhr_ctx *ctx, int nprob, const fhr_problem *probs,
+                                                const fhr_batch_params *prm, size_t *bytes);
+fhr_status fhr_reconstruct_batch(fhr_ctx *ctx, int nprob, const fhr_problem *probs,
+                                 const fhr_batch_params *prm, void *ws, size_t ws_bytes);
+fhr_status fhr_reconstruct_batch_autotune(fhr_ctx *ctx, int nprob, const fhr_problem *probs,
+                                          const fhr_batch_params *prm, void *ws, size_t ws_bytes,
+                                          int *best_tile);
+
+/* ------------------------------------------------------------------------
  * Subspace expansion -- Eq. (sub_expansion), x^h = x^s (D^s)^T.
  *   xs [N][N][Nr*K] float, D [Nk][K] float -> xh [Nr][N][N][Nk] in xh_dtype.
  * Bins k0..k1-1 only are written when 0 <= k0 < k1 <= Nk (a wavelength

@@ -9,26 +9,9 @@
 // and optional momentum z <- max(0, x+ + a_t (x+ - x)).
 #include <math.h>
 
-#include "proj.cuh"
+#include "mbir.cuh"
 
 namespace fhr {
-
-constexpr int kMbirMaxK = 8;
-
-struct MbirChan {
-    float inv_sv2[kMbirMaxK];   // 1 / sigma_v^2
-    float c0[kMbirMaxK];        // 1 / (T^(2-p) sigma_x^2)
-    float inv_tsx[kMbirMaxK];   // 1 / (T sigma_x)
-    float sv[kMbirMaxK], sx[kMbirMaxK];
-};
-
-struct MbirPrior {
-    float e;        // 2 - p
-    float c1;       // (2 - p) / p
-    float beta;
-    float b_edge, b_diag, b_slice;
-    float T, p;
-};
 
 __device__ __forceinline__ void chan_from_sigmas(MbirChan *c, int j, float sv, float sx, float T, float p) {
     c->sv[j] = sv;
@@ -37,10 +20,6 @@ __device__ __forceinline__ void chan_from_sigmas(MbirChan *c, int j, float sv, f
     c->c0[j] = (float)(1.0 / (pow((double)T, 2.0 - (double)p) * (double)sx * (double)sx));
     c->inv_tsx[j] = 1.f / (T * sx);
 }
-
-struct SigmaArgs {
-    float sv[kMbirMaxK], sx[kMbirMaxK];
-};
 
 __global__ void mbir_set_chan(SigmaArgs s, int K, float T, float p, MbirChan *out) {
     const int j = threadIdx.x;
@@ -102,19 +81,6 @@ __global__ void fill_kernel(float *x, int64_t n, float v) {
         x[i] = v;
 }
 
-// rho'(d)/d of the qGGMRF potential with q = 2:
-//   c0 / (1 + u) * (1 + c1 / (1 + u)),  u = (|d| / (T sx))^(2 - p)
-__device__ __forceinline__ float qggmrf_infl(float d, float c0, float inv_tsx, float e, float c1) {
-    float u;
-    if (e == 0.f) u = 1.f;
-    else {
-        const float a = fabsf(d) * inv_tsx;
-        u = a > 0.f ? exp2f(e * log2f(a)) : 0.f;
-    }
-    const float r = 1.f / (1.f + u);
-    return c0 * r * (1.f + c1 * r);
-}
-
 template <int VW>
 __global__ void __launch_bounds__(1024) mbir_update_kernel(const float *__restrict__ e, const float *__restrict__ z,
                                                            const float *__restrict__ xprev, float *__restrict__ xnew,
@@ -122,81 +88,12 @@ __global__ void __launch_bounds__(1024) mbir_update_kernel(const float *__restri
                                                            const float *__restrict__ dA, const MbirChan *__restrict__ chp,
                                                            MbirPrior pr, float mom_a, int N, int Nc, int Nv, int Nr,
                                                            int K, int Wl) {
-    using VF = VecF<VW>;
     const int CH = Wl / VW;
     const int ipb = blockDim.x / CH;
     const int pix = blockIdx.x * ipb + threadIdx.x / CH;
     const int ch = threadIdx.x % CH;
     if (threadIdx.x >= ipb * CH || pix >= N * N) return;
-    const typename VF::T bp = backproject_at<VW>(e, t, N, Nc, Nv, Wl, pix, ch);
-    const int iy = pix / N, ix = pix % N;
-    const size_t base = (size_t)pix * Wl + ch * VW;
-    const typename VF::T zc = VF::ld(z + base);
-    const float da = dA[pix];
-    float g[VW], d[VW];
-#pragma unroll
-    for (int q = 0; q < VW; ++q) {
-        const int j = (ch * VW + q) % K;
-        g[q] = -VF::get(bp, q) * chp->inv_sv2[j];
-        d[q] = da * chp->inv_sv2[j];
-    }
-    if (pr.beta != 0.f) {
-        const int dy8[8] = {-1, 1, 0, 0, -1, -1, 1, 1};
-        const int dx8[8] = {0, 0, -1, 1, -1, 1, -1, 1};
-#pragma unroll
-        for (int n = 0; n < 8; ++n) {
-            const int yy = iy + dy8[n], xx = ix + dx8[n];
-            if (yy < 0 || yy >= N || xx < 0 || xx >= N) continue;
-            const float b = pr.beta * (n < 4 ? pr.b_edge : pr.b_diag);
-            const typename VF::T zn = VF::ld(z + ((size_t)yy * N + xx) * Wl + ch * VW);
-#pragma unroll
-            for (int q = 0; q < VW; ++q) {
-                const int j = (ch * VW + q) % K;
-                const float dl = VF::get(zc, q) - VF::get(zn, q);
-                const float wt = qggmrf_infl(dl, chp->c0[j], chp->inv_tsx[j], pr.e, pr.c1);
-                g[q] = fmaf(b * dl, wt, g[q]);
-                d[q] = fmaf(2.f * b, wt, d[q]);
-            }
-        }
-        if (Nr > 1) {
-#pragma unroll
-            for (int q = 0; q < VW; ++q) {
-                const int w = ch * VW + q;
-                const int j = w % K, r = w / K;
-                const float b = pr.beta * pr.b_slice;
-                const float zq = VF::get(zc, q);
-                if (r > 0) {
-                    const float dl = zq - z[(size_t)pix * Wl + w - K];
-                    const float wt = qggmrf_infl(dl, chp->c0[j], chp->inv_tsx[j], pr.e, pr.c1);
-                    g[q] = fmaf(b * dl, wt, g[q]);
-                    d[q] = fmaf(2.f * b, wt, d[q]);
-                }
-                if (r < Nr - 1) {
-                    const float dl = zq - z[(size_t)pix * Wl + w + K];
-                    const float wt = qggmrf_infl(dl, chp->c0[j], chp->inv_tsx[j], pr.e, pr.c1);
-                    g[q] = fmaf(b * dl, wt, g[q]);
-                    d[q] = fmaf(2.f * b, wt, d[q]);
-                }
-            }
-        }
-    }
-    typename VF::T xn;
-#pragma unroll
-    for (int q = 0; q < VW; ++q) {
-        const float zq = VF::get(zc, q);
-        VF::set(xn, q, d[q] > 0.f ? fmaxf(0.f, zq - __fdiv_rn(g[q], d[q])) : zq);
-    }
-    VF::st(xnew + base, xn);
-    if (znext) {
-        const typename VF::T xp = VF::ld(xprev + base);
-        typename VF::T zz;
-#pragma unroll
-        for (int q = 0; q < VW; ++q) {
-            const float a = VF::get(xn, q);
-            VF::set(zz, q, fmaxf(0.f, fmaf(mom_a, a - VF::get(xp, q), a)));
-        }
-        VF::st(znext + base, zz);
-    }
+    mbir_update_at<VW>(e, z, xprev, xnew, znext, t, dA, chp, pr, mom_a, N, Nc, Nv, Nr, K, Wl, pix, ch);
 }
 
 struct MbirWs {
@@ -208,7 +105,6 @@ struct MbirWs {
     float *dA, *e, *buf[4];
 };
 
-constexpr int kSigBlocks = 128;
 
 static size_t carve_mbir(void *base, const fhr_geom *g, int K, MbirWs *w) {
     Carve c(base);

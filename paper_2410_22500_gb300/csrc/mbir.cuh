@@ -1,0 +1,129 @@
+// Shared pieces of the MBIR update (Eq. recon, SQS with the qGGMRF prior).
+#pragma once
+
+#include "proj.cuh"
+
+namespace fhr {
+
+constexpr int kMbirMaxK = 8;
+
+struct MbirChan {
+    float inv_sv2[kMbirMaxK];   // 1 / sigma_v^2
+    float c0[kMbirMaxK];        // 1 / (T^(2-p) sigma_x^2)
+    float inv_tsx[kMbirMaxK];   // 1 / (T sigma_x)
+    float sv[kMbirMaxK], sx[kMbirMaxK];
+};
+
+// Explicit per-channel sigmas (kernel argument).
+struct SigmaArgs {
+    float sv[kMbirMaxK], sx[kMbirMaxK];
+};
+
+// Blocks of the sigma reduction; fixed, so every caller sums in the same order.
+constexpr int kSigBlocks = 128;
+
+struct MbirPrior {
+    float e;        // 2 - p
+    float c1;       // (2 - p) / p
+    float beta;
+    float b_edge, b_diag, b_slice;
+    float T, p;
+};
+
+// rho'(d)/d of the qGGMRF potential with q = 2:
+//   c0 / (1 + u) * (1 + c1 / (1 + u)),  u = (|d| / (T sx))^(2 - p)
+__device__ __forceinline__ float qggmrf_infl(float d, float c0, float inv_tsx, float e, float c1) {
+    float u;
+    if (e == 0.f) u = 1.f;
+    else {
+        const float a = fabsf(d) * inv_tsx;
+        u = a > 0.f ? exp2f(e * log2f(a)) : 0.f;
+    }
+    const float r = 1.f / (1.f + u);
+    return c0 * r * (1.f + c1 * r);
+}
+
+// SQS update of one (pixel, channel chunk): x+ = max(0, z - g/d) with the data
+// term from the back-projected residual and the qGGMRF prior over the 8 in-plane
+// and (Nr > 1) 2 inter-slice neighbours; with znext, also the momentum point.
+// COH: e, z and xprev were written earlier in the same launch.
+template <int VW, bool COH = false>
+__device__ __forceinline__ void mbir_update_at(const float *__restrict__ e, const float *__restrict__ z,
+                                               const float *__restrict__ xprev, float *__restrict__ xnew,
+                                               float *__restrict__ znext, const ProjTables &t,
+                                               const float *__restrict__ dA, const MbirChan *__restrict__ chp,
+                                               const MbirPrior &pr, float mom_a, int N, int Nc, int Nv, int Nr, int K,
+                                               int Wl, int pix, int ch) {
+    using VF = VecF<VW>;
+    const typename VF::T bp = backproject_at<VW, COH>(e, t, N, Nc, Nv, Wl, pix, ch);
+    const int iy = pix / N, ix = pix % N;
+    const size_t base = (size_t)pix * Wl + ch * VW;
+    const typename VF::T zc = ldv<VW, COH>(z + base);
+    const float da = dA[pix];
+    float g[VW], d[VW];
+#pragma unroll
+    for (int q = 0; q < VW; ++q) {
+        const int j = (ch * VW + q) % K;
+        g[q] = -VF::get(bp, q) * chp->inv_sv2[j];
+        d[q] = da * chp->inv_sv2[j];
+    }
+    if (pr.beta != 0.f) {
+        const int dy8[8] = {-1, 1, 0, 0, -1, -1, 1, 1};
+        const int dx8[8] = {0, 0, -1, 1, -1, 1, -1, 1};
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            const int yy = iy + dy8[n], xx = ix + dx8[n];
+            if (yy < 0 || yy >= N || xx < 0 || xx >= N) continue;
+            const float b = pr.beta * (n < 4 ? pr.b_edge : pr.b_diag);
+            const typename VF::T zn = ldv<VW, COH>(z + ((size_t)yy * N + xx) * Wl + ch * VW);
+#pragma unroll
+            for (int q = 0; q < VW; ++q) {
+                const int j = (ch * VW + q) % K;
+                const float dl = VF::get(zc, q) - VF::get(zn, q);
+                const float wt = qggmrf_infl(dl, chp->c0[j], chp->inv_tsx[j], pr.e, pr.c1);
+                g[q] = fmaf(b * dl, wt, g[q]);
+                d[q] = fmaf(2.f * b, wt, d[q]);
+            }
+        }
+        if (Nr > 1) {
+#pragma unroll
+            for (int q = 0; q < VW; ++q) {
+                const int w = ch * VW + q;
+                const int j = w % K, r = w / K;
+                const float b = pr.beta * pr.b_slice;
+                const float zq = VF::get(zc, q);
+                if (r > 0) {
+                    const float dl = zq - ldv<1, COH>(z + (size_t)pix * Wl + w - K);
+                    const float wt = qggmrf_infl(dl, chp->c0[j], chp->inv_tsx[j], pr.e, pr.c1);
+                    g[q] = fmaf(b * dl, wt, g[q]);
+                    d[q] = fmaf(2.f * b, wt, d[q]);
+                }
+                if (r < Nr - 1) {
+                    const float dl = zq - ldv<1, COH>(z + (size_t)pix * Wl + w + K);
+                    const float wt = qggmrf_infl(dl, chp->c0[j], chp->inv_tsx[j], pr.e, pr.c1);
+                    g[q] = fmaf(b * dl, wt, g[q]);
+                    d[q] = fmaf(2.f * b, wt, d[q]);
+                }
+            }
+        }
+    }
+    typename VF::T xn;
+#pragma unroll
+    for (int q = 0; q < VW; ++q) {
+        const float zq = VF::get(zc, q);
+        VF::set(xn, q, d[q] > 0.f ? fmaxf(0.f, zq - __fdiv_rn(g[q], d[q])) : zq);
+    }
+    VF::st(xnew + base, xn);
+    if (znext) {
+        const typename VF::T xp = ldv<VW, COH>(xprev + base);
+        typename VF::T zz;
+#pragma unroll
+        for (int q = 0; q < VW; ++q) {
+            const float a = VF::get(xn, q);
+            VF::set(zz, q, fmaxf(0.f, fmaf(mom_a, a - VF::get(xp, q), a)));
+        }
+        VF::st(znext + base, zz);
+    }
+}
+
+}  // namespace fhr

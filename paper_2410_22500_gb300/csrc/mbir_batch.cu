@@ -1,0 +1,385 @@
+// Batched MBIR: every subspace channel and slice of many independent problems
+// of uneven size (Eq. recon for each) in ONE persistent cooperative launch,
+// replayed from a CUDA graph.  Each iteration is two grid-wide phases over a
+// flat list of work items (problem, range of rays / range of pixels):
+//   phase F: e = V - A z for every ray of every problem;
+//   phase B: the backward gather fused with the SQS update for every pixel;
+// separated by grid barriers whose waits are bounded (FHR_ERR_TIMEOUT).
+// The tile (rays or pixels per work item, in units of one block-wide sweep)
+// is chosen by an autotuner that times the candidates on the actual batch.
+#include <math.h>
+
+#include <vector>
+
+#include "mbir.cuh"
+
+namespace fhr {
+
+__global__ void mbir_sigma_kernel(const float *sino, int64_t rows, int K, double *part, unsigned *counter,
+                                  float snr_db, int Nc, float T, float p, MbirChan *out);
+__global__ void mbir_set_chan(SigmaArgs s, int K, float T, float p, MbirChan *out);
+__global__ void fill_kernel(float *x, int64_t n, float v);
+
+struct BatchProb {
+    int N, Nc, Nv, Nr, K, Wl;
+    ProjTables t;
+    const float *sino;
+    float *e, *buf[4], *dA;
+    MbirChan *chan;
+};
+
+struct BatchItem {
+    int q, start, count;
+};
+
+struct BatchArgs {
+    const BatchProb *probs;
+    const BatchItem *fitems, *bitems;
+    int nf, nb, iters, momentum;
+    const float *mom;       // [iters] momentum coefficients
+    MbirPrior pr;
+    unsigned *bar;          // [2]: arrival count, generation
+    int *status;
+};
+
+constexpr int kBatchThreads = 256;
+
+// Grid-wide barrier for a co-resident grid; the wait gives up after kWaitLimitNs.
+__device__ bool grid_barrier(unsigned *bar, int *status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            for (uint32_t n = 1; *gen == g; ++n) {
+                if ((n & 255u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) {
+                    report(status, FHR_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(kBatchThreads) mbir_batch_kernel(BatchArgs a) {
+    const int tid = threadIdx.x;
+    for (int it = 0; it < a.iters; ++it) {
+        const int par = it & 1;
+        // ---- phase F: residual e = V - A z
+        for (int f = blockIdx.x; f < a.nf; f += gridDim.x) {
+            const BatchItem item = a.fitems[f];
+            const BatchProb &P = a.probs[item.q];
+            const float *z = a.momentum ? P.buf[1 + 2 * par] : P.buf[par];
+            const int sweep = kBatchThreads / P.Wl;
+            const int ch = tid % P.Wl;
+            for (int r = tid / P.Wl; r < item.count && tid < sweep * P.Wl; r += sweep) {
+                const int row = item.start + r;
+                const float ax = forward_at<1, true>(z, P.t, P.N, P.Nc, P.Wl, row, ch);
+                const size_t o = (size_t)row * P.Wl + ch;
+                P.e[o] = P.sino[o] - ax;
+            }
+        }
+        if (!grid_barrier(a.bar, a.status)) return;
+        // ---- phase B: backward gather + SQS update (+ momentum)
+        for (int b = blockIdx.x; b < a.nb; b += gridDim.x) {
+            const BatchItem item = a.bitems[b];
+            const BatchProb &P = a.probs[item.q];
+            const int sweep = kBatchThreads / P.Wl;
+            const int ch = tid % P.Wl;
+            float *xprev = nullptr, *z, *xnew, *znext = nullptr;
+            if (a.momentum) {
+                xprev = P.buf[2 * par];
+                z = P.buf[1 + 2 * par];
+                xnew = P.buf[2 * (1 - par)];
+                znext = P.buf[1 + 2 * (1 - par)];
+            } else {
+                z = P.buf[par];
+                xnew = P.buf[1 - par];
+            }
+            for (int r = tid / P.Wl; r < item.count && tid < sweep * P.Wl; r += sweep)
+                mbir_update_at<1, true>(P.e, z, xprev, xnew, znext, P.t, P.dA, P.chan, a.pr, a.mom[it], P.N, P.Nc, P.Nv,
+                                  P.Nr, P.K, P.Wl, item.start + r, ch);
+        }
+        if (!grid_barrier(a.bar, a.status)) return;
+    }
+}
+
+// ---------------------------------------------------------------- host
+struct BatchWs {
+    int *status;
+    unsigned *bar;
+    unsigned *counter;
+    double *sig_part;
+    BatchProb *dprobs;
+    BatchItem *items;
+    float *mom;
+    char *per;   // per-problem region
+};
+
+static size_t prob_bytes(const fhr_problem &q, int K) {
+    Carve c(nullptr);
+    fhr_geom g{q.N, q.Nr, q.Nc, q.Nv, q.angles};
+    const int Wl = q.Nr * K;
+    proj_tables_carve(c, g.N, g.Nc, g.Nv, nullptr);
+    c.take<MbirChan>(1);
+    c.take<float>((size_t)q.N * q.N);                 // dA
+    c.take<float>((size_t)q.Nv * q.Nc * Wl);          // e
+    for (int i = 0; i < 4; ++i) c.take<float>((size_t)q.N * q.N * Wl);
+    return c.size();
+}
+
+static int64_t tile_rows(int Wl, int tile) { return (int64_t)tile * (kBatchThreads / Wl); }
+
+static size_t carve_batch(void *base, int nprob, const fhr_problem *probs, const fhr_batch_params *p, int tile,
+                          BatchWs *w, std::vector<BatchItem> *fi, std::vector<BatchItem> *bi) {
+    Carve c(base);
+    BatchWs t{};
+    t.status = c.take<int>(kStatusBytes / sizeof(int));
+    t.bar = c.take<unsigned>(4);
+    t.counter = c.take<unsigned>(4);
+    t.sig_part = c.take<double>((size_t)kSigBlocks * 2 * kMbirMaxK);
+    t.dprobs = c.take<BatchProb>((size_t)nprob);
+    // work items: enough room for the smallest tile (1)
+    int64_t nitems = 0;
+    for (int q = 0; q < nprob; ++q) {
+        const int Wl = probs[q].Nr * probs[q].K;
+        nitems += cdiv((int64_t)probs[q].Nv * probs[q].Nc, tile_rows(Wl, 1));
+        nitems += cdiv((int64_t)probs[q].N * probs[q].N, tile_rows(Wl, 1));
+    }
+    t.items = c.take<BatchItem>((size_t)nitems);
+    t.mom = c.take<float>((size_t)std::max(1, p->iters));
+    t.per = c.take<char>(0);
+    size_t per_total = 0;
+    for (int q = 0; q < nprob; ++q) per_total += prob_bytes(probs[q], probs[q].K) + 256;
+    c.take<char>(per_total);
+    if (w) *w = t;
+    if (fi && bi) {
+        fi->clear();
+        bi->clear();
+        for (int q = 0; q < nprob; ++q) {
+            const int Wl = probs[q].Nr * probs[q].K;
+            const int64_t tr = tile_rows(Wl, tile);
+            const int64_t nr = (int64_t)probs[q].Nv * probs[q].Nc, npx = (int64_t)probs[q].N * probs[q].N;
+            for (int64_t s = 0; s < nr; s += tr) fi->push_back({q, (int)s, (int)std::min<int64_t>(tr, nr - s)});
+            for (int64_t s = 0; s < npx; s += tr) bi->push_back({q, (int)s, (int)std::min<int64_t>(tr, npx - s)});
+        }
+    }
+    return c.size();
+}
+
+static fhr_status check_batch(fhr_ctx *ctx, int nprob, const fhr_problem *probs, const fhr_batch_params *p) {
+    FHR_ARG(nprob >= 1 && probs && p, "need at least one problem and params");
+    FHR_ARG(p->iters >= 0, "iters < 0");
+    if (p->q != 2.f) return set_error(ctx, FHR_ERR_UNSUPPORTED, "only q = 2 is implemented");
+    FHR_ARG(p->p >= 1.f && p->p <= 2.f && p->T > 0.f && p->beta >= 0.f, "bad prior parameters");
+    for (int q = 0; q < nprob; ++q) {
+        const fhr_problem &b = probs[q];
+        FHR_ARG(b.K >= 1 && b.K <= kMbirMaxK, "problem %d: K must be 1..8", q);
+        fhr_geom g{b.N, b.Nr, b.Nc, b.Nv, b.angles};
+        FHR_TRY(check_geom(ctx, &g, b.Nr * b.K));
+        FHR_ARG(b.Nr * b.K <= kBatchThreads, "problem %d: Nr*K must be <= %d in a batch", q, kBatchThreads);
+        FHR_ARG(b.sino && b.xs, "problem %d: null sinogram or volume", q);
+        FHR_ARG((b.Nr > 1) == (probs[0].Nr > 1), "a batch mixes 2-D and 3-D problems");
+        if (b.sigma_v[0] > 0.f && b.sigma_x[0] > 0.f)
+            for (int j = 0; j < b.K; ++j)
+                FHR_ARG(b.sigma_v[j] > 0.f && b.sigma_x[j] > 0.f, "problem %d: sigmas must be positive", q);
+    }
+    return FHR_OK;
+}
+
+static fhr_status batch_run(fhr_ctx *ctx, int nprob, const fhr_problem *probs, const fhr_batch_params *p, int tile,
+                            void *ws, size_t ws_bytes, bool write_back, float *ms_out) {
+    FHR_TRY(check_batch(ctx, nprob, probs, p));
+    FHR_ARG(ws && aligned(ws, 256), "workspace must be non-null and 256-byte aligned");
+    FHR_ARG(tile >= 1 && tile <= 64, "tile must be 1..64");
+    BatchWs w;
+    std::vector<BatchItem> fi, bi;
+    const size_t need = carve_batch(ws, nprob, probs, p, tile, &w, &fi, &bi);
+    FHR_ARG(ws_bytes >= need, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+    FHR_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    FHR_CUDA(cudaMemsetAsync(w.status, 0, kStatusBytes, st));
+    FHR_CUDA(cudaMemsetAsync(w.bar, 0, 4 * sizeof(unsigned), st));
+    FHR_CUDA(cudaMemsetAsync(w.counter, 0, 4 * sizeof(unsigned), st));
+
+    // per-problem set-up: tables, sigmas, A^T A 1, starting point
+    std::vector<BatchProb> hp((size_t)nprob);
+    MbirPrior pr;
+    pr.p = p->p;
+    pr.T = p->T;
+    pr.e = 2.f - p->p;
+    pr.c1 = (2.f - p->p) / p->p;
+    pr.beta = p->beta;
+    char *cur = w.per;
+    for (int q = 0; q < nprob; ++q) {
+        const fhr_problem &b = probs[q];
+        fhr_geom g{b.N, b.Nr, b.Nc, b.Nv, b.angles};
+        BatchProb &P = hp[(size_t)q];
+        P.N = b.N; P.Nc = b.Nc; P.Nv = b.Nv; P.Nr = b.Nr; P.K = b.K; P.Wl = b.Nr * b.K;
+        Carve c(cur);
+        proj_tables_carve(c, g.N, g.Nc, g.Nv, &P.t);
+        P.chan = c.take<MbirChan>(1);
+        P.dA = c.take<float>((size_t)b.N * b.N);
+        P.e = c.take<float>((size_t)b.Nv * b.Nc * P.Wl);
+        for (int i = 0; i < 4; ++i) P.buf[i] = c.take<float>((size_t)b.N * b.N * P.Wl);
+        P.sino = b.sino;
+        cur += round_up(c.size(), 256) + 256;
+        FHR_TRY(proj_build_tables(ctx, &g, P.t));
+        if (b.sigma_v[0] > 0.f && b.sigma_x[0] > 0.f) {
+            SigmaArgs s;
+            for (int j = 0; j < kMbirMaxK; ++j) {
+                s.sv[j] = j < b.K ? b.sigma_v[j] : 1.f;
+                s.sx[j] = j < b.K ? b.sigma_x[j] : 1.f;
+            }
+            mbir_set_chan<<<1, 32, 0, st>>>(s, b.K, p->T, p->p, P.chan);
+        } else {
+            mbir_sigma_kernel<<<kSigBlocks, 256, 0, st>>>(b.sino, (int64_t)b.Nv * b.Nc * b.Nr, b.K, w.sig_part, w.counter,
+                                                   p->snr_db, b.Nc, p->T, p->p, P.chan);
+        }
+        FHR_LAUNCHED();
+        fill_kernel<<<64, 256, 0, st>>>(P.buf[0], (int64_t)b.N * b.N, 1.f);
+        FHR_LAUNCHED();
+        FHR_TRY(proj_forward(ctx, &g, P.t, 1, P.buf[0], P.e, nullptr));
+        FHR_TRY(proj_backward(ctx, &g, P.t, 1, P.e, P.dA));
+        const size_t xb = sizeof(float) * (size_t)b.N * b.N * P.Wl;
+        FHR_CUDA(cudaMemcpyAsync(P.buf[0], b.xs, xb, cudaMemcpyDeviceToDevice, st));
+        if (p->momentum) FHR_CUDA(cudaMemcpyAsync(P.buf[1], b.xs, xb, cudaMemcpyDeviceToDevice, st));
+    }
+    // the weights' normalisation depends on the slice count; one batch shares Nr
+    const double r2 = 1.0 / sqrt(2.0);
+    const double z = 4.0 + 4.0 * r2 + (probs[0].Nr > 1 ? 2.0 : 0.0);
+    pr.b_edge = (float)(1.0 / z);
+    pr.b_diag = (float)(r2 / z);
+    pr.b_slice = (float)(1.0 / z);
+    std::vector<float> mom((size_t)std::max(1, p->iters), 0.f);
+    double tk = 1.0;
+    for (int i = 0; i < p->iters; ++i) {
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+        mom[(size_t)i] = p->momentum ? (float)((tk - 1.0) / tn) : 0.f;
+        tk = tn;
+    }
+    // small host tables travel with the stream (pageable copies are staged by the runtime)
+    std::vector<BatchItem> items(fi);
+    items.insert(items.end(), bi.begin(), bi.end());
+    FHR_CUDA(cudaMemcpyAsync(w.dprobs, hp.data(), sizeof(BatchProb) * hp.size(), cudaMemcpyHostToDevice, st));
+    FHR_CUDA(cudaMemcpyAsync(w.items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, st));
+    FHR_CUDA(cudaMemcpyAsync(w.mom, mom.data(), sizeof(float) * mom.size(), cudaMemcpyHostToDevice, st));
+
+    if (p->iters > 0) {
+        BatchArgs a;
+        a.probs = w.dprobs;
+        a.fitems = w.items;
+        a.nf = (int)fi.size();
+        a.bitems = w.items + fi.size();
+        a.nb = (int)bi.size();
+        a.iters = p->iters;
+        a.momentum = p->momentum;
+        a.mom = w.mom;
+        a.pr = pr;
+        a.bar = w.bar;
+        a.status = w.status;
+        int per_sm = 0;
+        FHR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mbir_batch_kernel, kBatchThreads, 0));
+        if (per_sm < 1) return set_error(ctx, FHR_ERR_UNSUPPORTED, "batch kernel does not fit an SM");
+        const int grid = std::min(ctx->sm_count * per_sm, std::max(a.nf, a.nb));
+        // one persistent cooperative launch, replayed from a CUDA graph
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+        FHR_CUDA(cudaGraphCreate(&graph, 0));
+        void *args[] = {&a};
+        cudaKernelNodeParams kp{};
+        kp.func = (void *)mbir_batch_kernel;
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(kBatchThreads);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        FHR_CUDA(cudaGraphAddKernelNode(&node, graph, nullptr, 0, &kp));
+        cudaLaunchAttributeValue coop{};
+        coop.cooperative = 1;
+        FHR_CUDA(cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &coop));
+        FHR_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (ms_out) {
+            FHR_CUDA(cudaEventCreate(&e0));
+            FHR_CUDA(cudaEventCreate(&e1));
+            FHR_CUDA(cudaEventRecord(e0, st));
+        }
+        FHR_CUDA(cudaGraphLaunch(exec, st));
+        ++ctx->launches;
+        if (ms_out) {
+            FHR_CUDA(cudaEventRecord(e1, st));
+            FHR_CUDA(cudaEventSynchronize(e1));
+            FHR_CUDA(cudaEventElapsedTime(ms_out, e0, e1));
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+        FHR_CUDA(cudaGraphExecDestroy(exec));
+        FHR_CUDA(cudaGraphDestroy(graph));
+    }
+    if (write_back) {
+        const int fin = p->iters & 1;
+        for (int q = 0; q < nprob; ++q) {
+            const BatchProb &P = hp[(size_t)q];
+            const float *src = p->momentum ? P.buf[2 * fin] : P.buf[fin];
+            FHR_CUDA(cudaMemcpyAsync(probs[q].xs, src, sizeof(float) * (size_t)P.N * P.N * P.Wl,
+                                     cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    return FHR_OK;
+}
+
+}  // namespace fhr
+
+using namespace fhr;
+
+extern "C" fhr_status fhr_reconstruct_batch_workspace_size(fhr_ctx *ctx, int nprob, const fhr_problem *probs,
+                                                           const fhr_batch_params *p, size_t *bytes) {
+    if (!ctx) return FHR_ERR_ARG;
+    FHR_TRY(check_batch(ctx, nprob, probs, p));
+    FHR_ARG(bytes, "bytes is null");
+    *bytes = carve_batch(nullptr, nprob, probs, p, 1, nullptr, nullptr, nullptr);
+    return FHR_OK;
+}
+
+extern "C" fhr_status fhr_reconstruct_batch(fhr_ctx *ctx, int nprob, const fhr_problem *probs,
+                                            const fhr_batch_params *p, void *ws, size_t ws_bytes) {
+    if (!ctx) return FHR_ERR_ARG;
+    FHR_ARG(p, "params is null");
+    return batch_run(ctx, nprob, probs, p, p->tile > 0 ? p->tile : 2, ws, ws_bytes, true, nullptr);
+}
+
+extern "C" fhr_status fhr_reconstruct_batch_autotune(fhr_ctx *ctx, int nprob, const fhr_problem *probs,
+                                                     const fhr_batch_params *p, void *ws, size_t ws_bytes,
+                                                     int *best_tile) {
+    if (!ctx) return FHR_ERR_ARG;
+    FHR_ARG(p && best_tile, "null argument");
+    fhr_batch_params q = *p;
+    q.iters = p->iters > 0 ? std::min(p->iters, 4) : 4;
+    float best = 1e30f;
+    int bt = 2;
+    const int cand[] = {1, 2, 4, 8, 16};
+    for (int t : cand) {
+        float ms = 0.f;
+        FHR_TRY(batch_run(ctx, nprob, probs, &q, t, ws, ws_bytes, false, &ms));
+        if (ms < best) {
+            best = ms;
+            bt = t;
+        }
+    }
+    *best_tile = bt;
+    return FHR_OK;
+}

@@ -30,6 +30,7 @@ template <>
 struct VecF<4> {
     using T = float4;
     __device__ __forceinline__ static float4 ld(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+    __device__ __forceinline__ static float4 ldcg(const float *p) { return __ldcg(reinterpret_cast<const float4 *>(p)); }
     __device__ __forceinline__ static void st(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
     __device__ __forceinline__ static void fma(float4 &a, float w, float4 x) {
         a.x = fmaf(w, x.x, a.x); a.y = fmaf(w, x.y, a.y); a.z = fmaf(w, x.z, a.z); a.w = fmaf(w, x.w, a.w);
@@ -44,12 +45,47 @@ template <>
 struct VecF<1> {
     using T = float;
     __device__ __forceinline__ static float ld(const float *p) { return *p; }
+    __device__ __forceinline__ static float ldcg(const float *p) { return __ldcg(p); }
     __device__ __forceinline__ static void st(float *p, float v) { *p = v; }
     __device__ __forceinline__ static void fma(float &a, float w, float x) { a = fmaf(w, x, a); }
     __device__ __forceinline__ static float zero() { return 0.f; }
     __device__ __forceinline__ static float get(const float &v, int) { return v; }
     __device__ __forceinline__ static void set(float &v, int, float f) { v = f; }
 };
+
+// Load of a vector the same launch may have written (COH: through L2 only,
+// never a possibly stale L1 line) or of data fixed for the launch.
+template <int VW, bool COH>
+__device__ __forceinline__ typename VecF<VW>::T ldv(const float *p) {
+    if constexpr (COH) return VecF<VW>::ldcg(p);
+    else return VecF<VW>::ld(p);
+}
+
+// sum over lines and candidates of A * x[pixel][w] for one ray (item = (v, c)),
+// chunk ch of VW values.
+template <int VW, bool COH = false>
+__device__ __forceinline__ typename VecF<VW>::T forward_at(const float *__restrict__ x, const ProjTables &t, int N,
+                                                           int Nc, int Wl, int item, int ch) {
+    using VF = VecF<VW>;
+    const int v = item / Nc;
+    const bool rows = t.rowmaj[v] != 0;
+    const float4 *fw = t.fw + (size_t)item * N;
+    const int *fs = t.fws + (size_t)item * N;
+    const int lstride = rows ? N : 1;     // pixel index = l * lstride + q * qstride
+    const int qstride = rows ? 1 : N;
+    typename VF::T acc = VF::zero();
+    const float *xc = x + ch * VW;
+    for (int l = 0; l < N; ++l) {
+        const float4 w = __ldg(fw + l);
+        const int s0 = __ldg(fs + l);
+        const int p0 = l * lstride + s0 * qstride;
+        if (w.x != 0.f) VF::fma(acc, w.x, ldv<VW, COH>(xc + (size_t)p0 * Wl));
+        if (w.y != 0.f) VF::fma(acc, w.y, ldv<VW, COH>(xc + (size_t)(p0 + qstride) * Wl));
+        if (w.z != 0.f) VF::fma(acc, w.z, ldv<VW, COH>(xc + (size_t)(p0 + 2 * qstride) * Wl));
+        if (w.w != 0.f) VF::fma(acc, w.w, ldv<VW, COH>(xc + (size_t)(p0 + 3 * qstride) * Wl));
+    }
+    return acc;
+}
 
 // y[v][c][w] = sum over lines and candidates of A * x[pixel][w].
 // Thread = (item (v, c), chunk of VW values).  With V non-null the output is
@@ -64,23 +100,7 @@ __global__ void __launch_bounds__(1024) proj_fwd_kernel(const float *__restrict_
     const int item = blockIdx.x * ipb + threadIdx.x / CH;
     const int ch = threadIdx.x % CH;
     if (threadIdx.x >= ipb * CH || item >= Nv * Nc) return;
-    const int v = item / Nc;
-    const bool rows = t.rowmaj[v] != 0;
-    const float4 *fw = t.fw + (size_t)item * N;
-    const int *fs = t.fws + (size_t)item * N;
-    const int lstride = rows ? N : 1;     // pixel index = l * lstride + q * qstride
-    const int qstride = rows ? 1 : N;
-    typename VF::T acc = VF::zero();
-    const float *xc = x + ch * VW;
-    for (int l = 0; l < N; ++l) {
-        const float4 w = __ldg(fw + l);
-        const int s0 = __ldg(fs + l);
-        const int p0 = l * lstride + s0 * qstride;
-        if (w.x != 0.f) VF::fma(acc, w.x, VF::ld(xc + (size_t)p0 * Wl));
-        if (w.y != 0.f) VF::fma(acc, w.y, VF::ld(xc + (size_t)(p0 + qstride) * Wl));
-        if (w.z != 0.f) VF::fma(acc, w.z, VF::ld(xc + (size_t)(p0 + 2 * qstride) * Wl));
-        if (w.w != 0.f) VF::fma(acc, w.w, VF::ld(xc + (size_t)(p0 + 3 * qstride) * Wl));
-    }
+    typename VF::T acc = forward_at<VW>(x, t, N, Nc, Wl, item, ch);
     float *yo = y + (size_t)item * Wl + ch * VW;
     if (V) {
         typename VF::T vv = VF::ld(V + (size_t)item * Wl + ch * VW);
@@ -91,7 +111,7 @@ __global__ void __launch_bounds__(1024) proj_fwd_kernel(const float *__restrict_
 }
 
 // x[pixel][w] = sum over views and candidate bins of A * y[v][c][w].
-template <int VW>
+template <int VW, bool COH = false>
 __device__ __forceinline__ typename VecF<VW>::T backproject_at(const float *__restrict__ y, const ProjTables &t, int N,
                                                                int Nc, int Nv, int Wl, int pix, int ch) {
     using VF = VecF<VW>;
@@ -101,9 +121,9 @@ __device__ __forceinline__ typename VecF<VW>::T backproject_at(const float *__re
     for (int v = 0; v < Nv; ++v) {
         const float4 w = __ldg(t.bk + v * NN + pix);
         const size_t row = (size_t)v * Nc + (int)w.w;
-        if (w.x != 0.f) VF::fma(acc, w.x, VF::ld(yc + row * Wl));
-        if (w.y != 0.f) VF::fma(acc, w.y, VF::ld(yc + (row + 1) * Wl));
-        if (w.z != 0.f) VF::fma(acc, w.z, VF::ld(yc + (row + 2) * Wl));
+        if (w.x != 0.f) VF::fma(acc, w.x, ldv<VW, COH>(yc + row * Wl));
+        if (w.y != 0.f) VF::fma(acc, w.y, ldv<VW, COH>(yc + (row + 1) * Wl));
+        if (w.z != 0.f) VF::fma(acc, w.z, ldv<VW, COH>(yc + (row + 2) * Wl));
     }
     return acc;
 }

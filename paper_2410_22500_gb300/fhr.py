@@ -24,6 +24,7 @@ ENTRY_POINTS = (
     "fhr_project", "fhr_backproject", "fhr_reconstruct_workspace_size", "fhr_reconstruct", "fhr_expand",
     "fhr_pipeline_workspace_size", "fhr_pipeline", "fhr_profile_enable", "fhr_profile_read",
     "fhr_decompose_static", "fhr_mlp_workspace_size", "fhr_mlp_forward", "fhr_mlp_grad", "fhr_mlp_adamw",
+    "fhr_reconstruct_batch_workspace_size", "fhr_reconstruct_batch", "fhr_reconstruct_batch_autotune",
 )
 
 
@@ -49,6 +50,18 @@ class MbirParams(ctypes.Structure):
                 ("T", ctypes.c_float), ("beta", ctypes.c_float), ("snr_db", ctypes.c_float),
                 ("momentum", ctypes.c_int), ("sigma_v", ctypes.POINTER(ctypes.c_float)),
                 ("sigma_x", ctypes.POINTER(ctypes.c_float))]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("Nr", ctypes.c_int), ("Nc", ctypes.c_int), ("Nv", ctypes.c_int),
+                ("K", ctypes.c_int), ("angles", ctypes.c_void_p), ("sino", ctypes.c_void_p), ("xs", ctypes.c_void_p),
+                ("sigma_v", ctypes.c_float * 8), ("sigma_x", ctypes.c_float * 8)]
+
+
+class BatchParams(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("p", ctypes.c_float), ("q", ctypes.c_float), ("T", ctypes.c_float),
+                ("beta", ctypes.c_float), ("snr_db", ctypes.c_float), ("momentum", ctypes.c_int),
+                ("tile", ctypes.c_int)]
 
 
 class MlpDims(ctypes.Structure):
@@ -106,6 +119,10 @@ def load():
         L.fhr_mlp_forward.argtypes = [vp, ctypes.POINTER(MlpDims), vp, ctypes.c_int64, vp, vp, vp, sz]
         L.fhr_mlp_grad.argtypes = [vp, ctypes.POINTER(MlpDims), vp, ctypes.c_int64, vp, vp, vp, vp, vp, sz]
         L.fhr_mlp_adamw.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.c_int] + [ctypes.c_float] * 5
+        PP, BP = ctypes.POINTER(Problem), ctypes.POINTER(BatchParams)
+        L.fhr_reconstruct_batch_workspace_size.argtypes = [vp, ctypes.c_int, PP, BP, szp]
+        L.fhr_reconstruct_batch.argtypes = [vp, ctypes.c_int, PP, BP, vp, sz]
+        L.fhr_reconstruct_batch_autotune.argtypes = [vp, ctypes.c_int, PP, BP, vp, sz, ctypes.POINTER(ctypes.c_int)]
         L.fhr_profile_enable.argtypes = [vp, ctypes.c_int]
         L.fhr_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_double)]
@@ -298,6 +315,58 @@ class Context:
         if check_status:
             self.check(self.status(ws))
         return xs
+
+    # ------------------------------------------------------------ batched MBIR
+    @staticmethod
+    def batch_problems(sinos, Ns, Ks, xss, *, Nr=1, angles=None, sigmas=None):
+        """Problem array for fhr_reconstruct_batch; sinos[i] [Nv][Nc][Nr*K] and
+        xss[i] [N][N][Nr*K] are device tensors, Nr an int or one per problem,
+        sigmas[i] = (sigma_v, sigma_x) or None."""
+        n = len(sinos)
+        Nrs = list(Nr) if isinstance(Nr, (list, tuple)) else [Nr] * n
+        arr = (Problem * n)()
+        for i in range(n):
+            s = sinos[i]
+            arr[i].N, arr[i].Nr, arr[i].Nc, arr[i].Nv, arr[i].K = Ns[i], Nrs[i], s.shape[1], s.shape[0], Ks[i]
+            arr[i].angles = None if angles is None or angles[i] is None else angles[i].data_ptr()
+            arr[i].sino = s.data_ptr()
+            arr[i].xs = xss[i].data_ptr()
+            if sigmas is not None and sigmas[i] is not None:
+                for j in range(Ks[i]):
+                    arr[i].sigma_v[j] = float(sigmas[i][0][j])
+                    arr[i].sigma_x[j] = float(sigmas[i][1][j])
+        return arr
+
+    @staticmethod
+    def batch_params(iters, p=1.2, q=2.0, T=1.0, beta=1.0, snr_db=30.0, momentum=False, tile=0):
+        return BatchParams(iters, p, q, T, beta, snr_db, int(momentum), tile)
+
+    def reconstruct_batch(self, sinos, Ns, Ks, iters, *, Nr=1, xss=None, angles=None, sigmas=None, tile=0,
+                          autotune=False, check_status=True, **kw):
+        """Eq. (recon) for every problem of the batch in one persistent launch.
+        Returns (xss, tile used)."""
+        torch = _torch()
+        Nrs = list(Nr) if isinstance(Nr, (list, tuple)) else [Nr] * len(sinos)
+        if xss is None:
+            xss = [torch.zeros((N, N, r * K), dtype=torch.float32, device=s.device)
+                   for s, N, K, r in zip(sinos, Ns, Ks, Nrs)]
+        arr = self.batch_problems(sinos, Ns, Ks, xss, Nr=Nr, angles=angles, sigmas=sigmas)
+        prm = self.batch_params(iters, tile=tile, **kw)
+        n = ctypes.c_size_t()
+        self.check(self.L.fhr_reconstruct_batch_workspace_size(self._h, len(sinos), arr, ctypes.byref(prm),
+                                                               ctypes.byref(n)))
+        ws = self.workspace(n.value)
+        if autotune:
+            best = ctypes.c_int()
+            self.check(self.L.fhr_reconstruct_batch_autotune(self._h, len(sinos), arr, ctypes.byref(prm), _ptr(ws),
+                                                             n.value, ctypes.byref(best)))
+            if check_status:
+                self.check(self.status(ws))
+            prm.tile = best.value
+        self.check(self.L.fhr_reconstruct_batch(self._h, len(sinos), arr, ctypes.byref(prm), _ptr(ws), n.value))
+        if check_status:
+            self.check(self.status(ws))
+        return xss, (prm.tile or 2)
 
     # ------------------------------------------------------------ expand
     def expand(self, xs, D, N, Nr, *, k0=0, k1=0, xh_dtype=F32, xh=None):
