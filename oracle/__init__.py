@@ -15,6 +15,9 @@ Every function cites the passage of the paper it follows.  Parity status:
   expansion        pinned (identity dictionary, commutes with the projector)
   MLP warm start   pinned (closed-form activations, layer-wise numpy, central
                    differences of the loss, AdamW closed form)
+  clustering start pinned (published splitmix64 outputs, separated clusters
+                   converge to their label means, monotone Lloyd cost, K = 1
+                   mean, zero-distance samples never seeded, K = 1 V step)
 """
 from __future__ import annotations
 
@@ -79,6 +82,13 @@ def lib():
             L.or_mbir.argtypes = [ctypes.c_int] * 5 + [_dp, _dp, _dp, _dp, ctypes.POINTER(_MbirParams), _dp, _dp]
             L.or_mbir_sigmas.argtypes = [ctypes.c_long, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp]
             L.or_expand.argtypes = [ctypes.c_int] * 4 + [_dp, _dp, _dp]
+            vp = ctypes.c_void_p
+            L.or_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_int, vp]
+            L.or_splitmix64.restype = None
+            L.or_kmeans.argtypes = [ctypes.c_long, ctypes.c_int, _dp, ctypes.c_long, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_uint64, _dp, vp, _dp, vp]
+            L.or_cluster_init.argtypes = [ctypes.c_long, ctypes.c_int, _dp, ctypes.c_long, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_uint64, _dp, _dp]
         return _lib
 
 
@@ -195,6 +205,42 @@ def nndsvd(P, K):
     """NNDSVD initialisation of P (Np x Nk) from numpy's exact SVD."""
     U, S, Vt = np.linalg.svd(_f64(P), full_matrices=False)
     return nndsvd_split(U[:, :K], S[:K], Vt[:K, :], K)
+
+
+def splitmix64(seed, n):
+    """The first n outputs of splitmix64 started from state `seed`."""
+    out = np.zeros(n, dtype=np.uint64)
+    lib().or_splitmix64(ctypes.c_uint64(seed), n, out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def kmeans(P, S, K, iters, seed):
+    """k-means of the sampled rows of P (the clustering start's first three steps).
+    Returns (centres [K][Nk], labels [S], cost [iters+1], seeds [K])."""
+    P = _f64(P)
+    Np, Nk = P.shape
+    C = np.zeros((K, Nk))
+    lab = np.zeros(S, dtype=np.int32)
+    cost = np.zeros(iters + 1)
+    seeds = np.zeros(K, dtype=np.int64)
+    rc = lib().or_kmeans(Np, Nk, _d(P), S, K, iters, ctypes.c_uint64(seed), _d(C),
+                         lab.ctypes.data_as(ctypes.c_void_p), _d(cost), seeds.ctypes.data_as(ctypes.c_void_p))
+    if rc:
+        raise ValueError("or_kmeans failed: %d" % rc)
+    return C, lab, cost, seeds
+
+
+def cluster_init(P, K, S=None, iters=20, seed=0):
+    """Clustering start: D0 [Nk][K] = k-means centres, W0 [Np][K] = one HALS V step from 0."""
+    P = _f64(P)
+    Np, Nk = P.shape
+    S = min(Np, 32768) if S is None else S
+    D0 = np.zeros((Nk, K))
+    W0 = np.zeros((Np, K))
+    rc = lib().or_cluster_init(Np, Nk, _d(P), S, K, iters, ctypes.c_uint64(seed), _d(D0), _d(W0))
+    if rc:
+        raise ValueError("or_cluster_init failed: %d" % rc)
+    return D0, W0
 
 
 # ---------------------------------------------------------------- projector

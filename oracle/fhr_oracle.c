@@ -209,6 +209,142 @@ int or_nmf(long Np, int Nk, int K, int iters, const double *P, double *D, double
 }
 
 /* ------------------------------------------------------------------------
+ * Clustering start for the NMF (not specified by the paper, whose Sec. III
+ * uses NNDSVD; this is the library's added "clustering-initialised" mode).
+ * Reading, stated in full because the paper gives none:
+ *   1. sample S pixels, j_i = floor(i * Np / S), i = 0..S-1;
+ *   2. k-means++ seeding: u_m is output m (0-based) of splitmix64 (Steele, Lea
+ *      and Flood, OOPSLA 2014) started from state `seed`, scaled to [0, 1) by
+ *      its top 53 bits.  Centre 0 is sample floor(u_0 S).  Centre m >= 1 is the
+ *      first sample i whose running sum of d_i exceeds u_m * sum(d), where d_i
+ *      is the squared distance of sample i to its nearest chosen centre (if
+ *      every d_i is 0: sample floor(u_m S));
+ *   3. `iters` Lloyd iterations: assign each sample to its nearest centre
+ *      (lowest index on ties), then move each centre to the mean of its
+ *      samples (a centre with no samples stays where it is);
+ *   4. D0 column m = centre m; W0 = one HALS V half-step started from V = 0.
+ * All distances and means in FP64.
+ * ---------------------------------------------------------------------- */
+static uint64_t splitmix64_next(uint64_t *state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* the first n outputs of splitmix64 from `seed` */
+void or_splitmix64(uint64_t seed, int n, uint64_t *out)
+{
+    uint64_t st = seed;
+    for (int i = 0; i < n; ++i) out[i] = splitmix64_next(&st);
+}
+
+static double sqdist(const double *a, const double *b, int n)
+{
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double d = a[k] - b[k];
+        s += d * d;
+    }
+    return s;
+}
+
+/* k-means on the sampled rows of P [Np][Nk].  C [K][Nk] receives the centres,
+ * labels [S] (if non-NULL) the final assignment, cost [iters+1] (if non-NULL)
+ * the sum of squared distances to the assigned centre before each centre
+ * move and after the last one, seeds [K] (if non-NULL) the seeding samples. */
+int or_kmeans(long Np, int Nk, const double *P, long S, int K, int iters, uint64_t seed, double *C,
+              int *labels, double *cost, long *seeds)
+{
+    if (S < 1 || S > Np || K < 1 || K > S) return OR_ERR_ARG;
+    double *X = (double *)malloc((size_t)S * Nk * sizeof(double));
+    double *d = (double *)malloc((size_t)S * sizeof(double));
+    int *lab = (int *)malloc((size_t)S * sizeof(int));
+    double *acc = (double *)malloc((size_t)K * Nk * sizeof(double));
+    long *cnt = (long *)malloc((size_t)K * sizeof(long));
+    if (!X || !d || !lab || !acc || !cnt) {
+        free(X); free(d); free(lab); free(acc); free(cnt);
+        return OR_ERR_NOMEM;
+    }
+    for (long i = 0; i < S; ++i) {
+        long j = (long)(((__int128)i * Np) / S);
+        memcpy(X + (size_t)i * Nk, P + (size_t)j * Nk, (size_t)Nk * sizeof(double));
+    }
+    /* k-means++ seeding */
+    uint64_t st = seed;
+    for (int m = 0; m < K; ++m) {
+        double u = (double)(splitmix64_next(&st) >> 11) * 0x1.0p-53;
+        long pick = (long)(u * (double)S);
+        if (m > 0) {
+            for (long i = 0; i < S; ++i) {
+                double e = sqdist(X + (size_t)i * Nk, C + (size_t)(m - 1) * Nk, Nk);
+                d[i] = (m == 1 || e < d[i]) ? e : d[i];
+            }
+            double tot = 0.0;
+            for (long i = 0; i < S; ++i) tot += d[i];
+            if (tot > 0.0) {
+                double target = u * tot, run = 0.0;
+                pick = -1;
+                for (long i = 0; i < S; ++i) {
+                    run += d[i];
+                    if (run > target) { pick = i; break; }
+                }
+                if (pick < 0)  /* rounding: the last sample with d > 0 */
+                    for (long i = S - 1; i >= 0; --i)
+                        if (d[i] > 0.0) { pick = i; break; }
+            }
+        }
+        if (seeds) seeds[m] = pick;
+        memcpy(C + (size_t)m * Nk, X + (size_t)pick * Nk, (size_t)Nk * sizeof(double));
+    }
+    /* Lloyd iterations */
+    for (int it = 0; it <= iters; ++it) {
+        double c = 0.0;
+        for (long i = 0; i < S; ++i) {
+            int best = 0;
+            double bd = sqdist(X + (size_t)i * Nk, C, Nk);
+            for (int m = 1; m < K; ++m) {
+                double e = sqdist(X + (size_t)i * Nk, C + (size_t)m * Nk, Nk);
+                if (e < bd) { bd = e; best = m; }
+            }
+            lab[i] = best;
+            c += bd;
+        }
+        if (cost) cost[it] = c;
+        if (it == iters) break;
+        memset(acc, 0, (size_t)K * Nk * sizeof(double));
+        memset(cnt, 0, (size_t)K * sizeof(long));
+        for (long i = 0; i < S; ++i) {
+            cnt[lab[i]]++;
+            for (int k = 0; k < Nk; ++k) acc[(size_t)lab[i] * Nk + k] += X[(size_t)i * Nk + k];
+        }
+        for (int m = 0; m < K; ++m)
+            if (cnt[m] > 0)
+                for (int k = 0; k < Nk; ++k) C[(size_t)m * Nk + k] = acc[(size_t)m * Nk + k] / (double)cnt[m];
+    }
+    if (labels) memcpy(labels, lab, (size_t)S * sizeof(int));
+    free(X); free(d); free(lab); free(acc); free(cnt);
+    return OR_OK;
+}
+
+/* Clustering start: D0 [Nk][K] = k-means centres (transposed), W0 [Np][K] =
+ * one HALS V half-step from zero with D0. */
+int or_cluster_init(long Np, int Nk, const double *P, long S, int K, int iters, uint64_t seed, double *D0,
+                    double *W0)
+{
+    double *C = (double *)malloc((size_t)K * Nk * sizeof(double));
+    if (!C) return OR_ERR_NOMEM;
+    int e = or_kmeans(Np, Nk, P, S, K, iters, seed, C, NULL, NULL, NULL);
+    if (e) { free(C); return e; }
+    for (int k = 0; k < Nk; ++k)
+        for (int m = 0; m < K; ++m) D0[(size_t)k * K + m] = C[(size_t)m * Nk + k];
+    free(C);
+    memset(W0, 0, (size_t)Np * K * sizeof(double));
+    return or_hals_update_W(Np, Nk, K, P, D0, W0);
+}
+
+/* ------------------------------------------------------------------------
  * Parallel-beam projector A of Eq. (porj_matd_rel) / Eq. (recon).  The paper
  * does not state its discretisation (it uses a library).  Reading: the strip
  * (area) model.  A_{(v,c),i} = area(pixel_i  intersect  strip_{v,c}) / du, with
