@@ -128,6 +128,16 @@ fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *prm,
  *         mlp->ldx == ldP, mlp->x_dtype == p_dtype), one pass with W0 fixed
  *         for P^T W0 and W0^T W0, then D0 from ten HALS D half-steps from
  *         D = 0; the iterations then run as from a GIVEN start.
+ *         FHR_INIT_CLUSTER (the "clustering-initialised" start; the paper's
+ *         Sec. III uses NNDSVD): k-means on the pixel sample
+ *         j_i = floor(i Np / S), i < S = min(Np, kmeans_samples or 32768):
+ *         k-means++ seeding (u_m = output m of splitmix64 from `seed`, top
+ *         53 bits; centre 0 = sample floor(u_0 S), centre m = first sample
+ *         whose running sum of squared distances to the nearest chosen centre
+ *         exceeds u_m times their total), kmeans_iters (0: 20) Lloyd
+ *         iterations (nearest centre, lowest index on ties; an empty cluster
+ *         keeps its centre), all in FP64; D0 = the centres, W0 = one HALS V
+ *         half-step from V = 0; the iterations then run as from GIVEN.
  *   P     [Np][ldP] in p_dtype; D [Nk][K] and W [Np][K] float, in/out.
  *   obj   device double [iters] or NULL: ||p - V D^T||^2 after each
  *         iteration, from the Gram identity in double precision.
@@ -136,6 +146,7 @@ fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *prm,
 #define FHR_INIT_GIVEN 0
 #define FHR_INIT_NNDSVD 1
 #define FHR_INIT_LEARNED 2
+#define FHR_INIT_CLUSTER 3
 
 struct fhr_mlp_dims_s;
 
@@ -150,6 +161,10 @@ typedef struct {
     /* FHR_INIT_LEARNED only: the warm-start network (see fhr_mlp_forward) */
     const struct fhr_mlp_dims_s *mlp;
     const float *mlp_params;
+    /* FHR_INIT_CLUSTER only: pixel samples (0: 32768; at most 2^20) and
+     * Lloyd iterations (0: 20) */
+    int64_t kmeans_samples;
+    int kmeans_iters;
 } fhr_nmf_params;
 
 fhr_status fhr_decompose_workspace_size(fhr_ctx *ctx, const fhr_nmf_params *prm, size_t *bytes);
@@ -236,7 +251,8 @@ fhr_status fhr_reconstruct(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_param
  * a CUDA graph), two grid-wide phases per iteration (forward residual; fused
  * backward gather + SQS update) separated by bounded grid barriers.
  * probs is a HOST array; each problem's sinogram/volume are device pointers
- * with the layouts of fhr_reconstruct (Wl = Nr*K <= 256); sigma_v[0] > 0 and
+ * with the layouts of fhr_reconstruct (Wl = Nr*K <= 256; the sinogram 16-byte
+ * aligned when Wl % 4 == 0, 8-byte when Wl % 2 == 0); sigma_v[0] > 0 and
  * sigma_x[0] > 0 select explicit per-channel sigmas, else the defaults of
  * fhr_reconstruct.  All problems share the prior parameters and iteration
  * count, and must all be 2-D (Nr = 1) or all 3-D.

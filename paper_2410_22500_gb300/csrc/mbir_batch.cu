@@ -9,6 +9,7 @@
 // is chosen by an autotuner that times the candidates on the actual batch.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "mbir.cuh"
@@ -39,6 +40,7 @@ struct BatchArgs {
     const float *mom;       // [iters] momentum coefficients
     MbirPrior pr;
     unsigned *bar;          // [2]: arrival count, generation
+    unsigned *ctr;          // [2 * iters]: next work item of each phase
     int *status;
 };
 
@@ -74,31 +76,68 @@ __device__ bool grid_barrier(unsigned *bar, int *status) {
     return ok != 0;
 }
 
+// Values per thread for a problem's Wl (all Wl values of a pixel / ray are
+// one contiguous vector; host and device agree on this split).
+__host__ __device__ inline int batch_vw(int Wl) { return Wl % 4 == 0 ? 4 : (Wl % 2 == 0 ? 2 : 1); }
+__host__ __device__ inline int batch_sweep(int Wl) { return kBatchThreads / (Wl / batch_vw(Wl)); }
+
+template <int VW>
+__device__ __forceinline__ void batch_forward(const BatchItem &item, const BatchProb &P, const float *z) {
+    using VF = VecF<VW>;
+    const int CH = P.Wl / VW, sweep = kBatchThreads / CH;
+    const int tid = threadIdx.x, ch = tid % CH;
+    if (tid >= sweep * CH) return;
+    for (int r = tid / CH; r < item.count; r += sweep) {
+        const int row = item.start + r;
+        typename VF::T ax = forward_at<VW, true>(z, P.t, P.N, P.Nc, P.Wl, row, ch);
+        const size_t o = (size_t)row * P.Wl + ch * VW;
+        const typename VF::T v = VF::ld(P.sino + o);
+#pragma unroll
+        for (int e = 0; e < VW; ++e) VF::set(ax, e, VF::get(v, e) - VF::get(ax, e));
+        VF::st(P.e + o, ax);
+    }
+}
+
+template <int VW>
+__device__ __forceinline__ void batch_update(const BatchItem &item, const BatchProb &P, const float *xprev,
+                                             const float *z, float *xnew, float *znext, const MbirPrior &pr,
+                                             float mom) {
+    const int CH = P.Wl / VW, sweep = kBatchThreads / CH;
+    const int tid = threadIdx.x, ch = tid % CH;
+    if (tid >= sweep * CH) return;
+    for (int r = tid / CH; r < item.count; r += sweep)
+        mbir_update_at<VW, true>(P.e, z, xprev, xnew, znext, P.t, P.dA, P.chan, pr, mom, P.N, P.Nc, P.Nv, P.Nr, P.K,
+                                 P.Wl, item.start + r, ch);
+}
+
+// Next work item of a phase: items are taken in list order (largest first)
+// from a per-phase counter, so uneven items balance across the grid.
+__device__ __forceinline__ int next_item(unsigned *ctr) {
+    __shared__ int idx;
+    __syncthreads();
+    if (threadIdx.x == 0) idx = (int)atomicAdd(ctr, 1u);
+    __syncthreads();
+    return idx;
+}
+
 __global__ void __launch_bounds__(kBatchThreads) mbir_batch_kernel(BatchArgs a) {
-    const int tid = threadIdx.x;
     for (int it = 0; it < a.iters; ++it) {
         const int par = it & 1;
         // ---- phase F: residual e = V - A z
-        for (int f = blockIdx.x; f < a.nf; f += gridDim.x) {
+        for (int f = next_item(a.ctr + 2 * it); f < a.nf; f = next_item(a.ctr + 2 * it)) {
             const BatchItem item = a.fitems[f];
             const BatchProb &P = a.probs[item.q];
             const float *z = a.momentum ? P.buf[1 + 2 * par] : P.buf[par];
-            const int sweep = kBatchThreads / P.Wl;
-            const int ch = tid % P.Wl;
-            for (int r = tid / P.Wl; r < item.count && tid < sweep * P.Wl; r += sweep) {
-                const int row = item.start + r;
-                const float ax = forward_at<1, true>(z, P.t, P.N, P.Nc, P.Wl, row, ch);
-                const size_t o = (size_t)row * P.Wl + ch;
-                P.e[o] = P.sino[o] - ax;
-            }
+            const int vw = batch_vw(P.Wl);
+            if (vw == 4) batch_forward<4>(item, P, z);
+            else if (vw == 2) batch_forward<2>(item, P, z);
+            else batch_forward<1>(item, P, z);
         }
         if (!grid_barrier(a.bar, a.status)) return;
         // ---- phase B: backward gather + SQS update (+ momentum)
-        for (int b = blockIdx.x; b < a.nb; b += gridDim.x) {
+        for (int b = next_item(a.ctr + 2 * it + 1); b < a.nb; b = next_item(a.ctr + 2 * it + 1)) {
             const BatchItem item = a.bitems[b];
             const BatchProb &P = a.probs[item.q];
-            const int sweep = kBatchThreads / P.Wl;
-            const int ch = tid % P.Wl;
             float *xprev = nullptr, *z, *xnew, *znext = nullptr;
             if (a.momentum) {
                 xprev = P.buf[2 * par];
@@ -109,9 +148,10 @@ __global__ void __launch_bounds__(kBatchThreads) mbir_batch_kernel(BatchArgs a) 
                 z = P.buf[par];
                 xnew = P.buf[1 - par];
             }
-            for (int r = tid / P.Wl; r < item.count && tid < sweep * P.Wl; r += sweep)
-                mbir_update_at<1, true>(P.e, z, xprev, xnew, znext, P.t, P.dA, P.chan, a.pr, a.mom[it], P.N, P.Nc, P.Nv,
-                                  P.Nr, P.K, P.Wl, item.start + r, ch);
+            const int vw = batch_vw(P.Wl);
+            if (vw == 4) batch_update<4>(item, P, xprev, z, xnew, znext, a.pr, a.mom[it]);
+            else if (vw == 2) batch_update<2>(item, P, xprev, z, xnew, znext, a.pr, a.mom[it]);
+            else batch_update<1>(item, P, xprev, z, xnew, znext, a.pr, a.mom[it]);
         }
         if (!grid_barrier(a.bar, a.status)) return;
     }
@@ -126,6 +166,7 @@ struct BatchWs {
     BatchProb *dprobs;
     BatchItem *items;
     float *mom;
+    unsigned *ctr;
     char *per;   // per-problem region
 };
 
@@ -141,7 +182,7 @@ static size_t prob_bytes(const fhr_problem &q, int K) {
     return c.size();
 }
 
-static int64_t tile_rows(int Wl, int tile) { return (int64_t)tile * (kBatchThreads / Wl); }
+static int64_t tile_rows(int Wl, int tile) { return (int64_t)tile * batch_sweep(Wl); }
 
 static size_t carve_batch(void *base, int nprob, const fhr_problem *probs, const fhr_batch_params *p, int tile,
                           BatchWs *w, std::vector<BatchItem> *fi, std::vector<BatchItem> *bi) {
@@ -161,6 +202,7 @@ static size_t carve_batch(void *base, int nprob, const fhr_problem *probs, const
     }
     t.items = c.take<BatchItem>((size_t)nitems);
     t.mom = c.take<float>((size_t)std::max(1, p->iters));
+    t.ctr = c.take<unsigned>((size_t)2 * std::max(1, p->iters));
     t.per = c.take<char>(0);
     size_t per_total = 0;
     for (int q = 0; q < nprob; ++q) per_total += prob_bytes(probs[q], probs[q].K) + 256;
@@ -176,6 +218,16 @@ static size_t carve_batch(void *base, int nprob, const fhr_problem *probs, const
             for (int64_t s = 0; s < nr; s += tr) fi->push_back({q, (int)s, (int)std::min<int64_t>(tr, nr - s)});
             for (int64_t s = 0; s < npx; s += tr) bi->push_back({q, (int)s, (int)std::min<int64_t>(tr, npx - s)});
         }
+        // largest items first (work per item ~ block sweeps x gather length x values per thread)
+        auto cost = [&](const BatchItem &it, bool fwd) {
+            const fhr_problem &b = probs[it.q];
+            const int Wl = b.Nr * b.K, sw = batch_sweep(Wl);
+            return (int64_t)((it.count + sw - 1) / sw) * (fwd ? b.N : b.Nv + 9) * batch_vw(Wl);
+        };
+        std::stable_sort(fi->begin(), fi->end(),
+                         [&](const BatchItem &x, const BatchItem &y) { return cost(x, true) > cost(y, true); });
+        std::stable_sort(bi->begin(), bi->end(),
+                         [&](const BatchItem &x, const BatchItem &y) { return cost(x, false) > cost(y, false); });
     }
     return c.size();
 }
@@ -192,6 +244,8 @@ static fhr_status check_batch(fhr_ctx *ctx, int nprob, const fhr_problem *probs,
         FHR_TRY(check_geom(ctx, &g, b.Nr * b.K));
         FHR_ARG(b.Nr * b.K <= kBatchThreads, "problem %d: Nr*K must be <= %d in a batch", q, kBatchThreads);
         FHR_ARG(b.sino && b.xs, "problem %d: null sinogram or volume", q);
+        FHR_ARG(aligned(b.sino, 4 * (size_t)batch_vw(b.Nr * b.K)), "problem %d: sinogram not aligned to %d bytes", q,
+                4 * batch_vw(b.Nr * b.K));
         FHR_ARG((b.Nr > 1) == (probs[0].Nr > 1), "a batch mixes 2-D and 3-D problems");
         if (b.sigma_v[0] > 0.f && b.sigma_x[0] > 0.f)
             for (int j = 0; j < b.K; ++j)
@@ -213,6 +267,7 @@ static fhr_status batch_run(fhr_ctx *ctx, int nprob, const fhr_problem *probs, c
     cudaStream_t st = ctx->stream;
     FHR_CUDA(cudaMemsetAsync(w.status, 0, kStatusBytes, st));
     FHR_CUDA(cudaMemsetAsync(w.bar, 0, 4 * sizeof(unsigned), st));
+    FHR_CUDA(cudaMemsetAsync(w.ctr, 0, sizeof(unsigned) * 2 * (size_t)std::max(1, p->iters), st));
     FHR_CUDA(cudaMemsetAsync(w.counter, 0, 4 * sizeof(unsigned), st));
 
     // per-problem set-up: tables, sigmas, A^T A 1, starting point
@@ -290,6 +345,7 @@ static fhr_status batch_run(fhr_ctx *ctx, int nprob, const fhr_problem *probs, c
         a.mom = w.mom;
         a.pr = pr;
         a.bar = w.bar;
+        a.ctr = w.ctr;
         a.status = w.status;
         int per_sm = 0;
         FHR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mbir_batch_kernel, kBatchThreads, 0));

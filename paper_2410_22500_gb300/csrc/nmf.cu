@@ -252,6 +252,8 @@ __global__ void nmf_finalize(const double *D64, const NmfState *st, int Nk, int 
 }
 
 // ---------------------------------------------------------------- host
+fhr_status cluster_check(fhr_ctx *ctx, const fhr_nmf_params *p);
+
 static fhr_status check_nmf(fhr_ctx *ctx, const fhr_nmf_params *p) {
     FHR_ARG(p, "params is null");
     FHR_ARG(p->Np > 0 && p->Nk > 0, "Np and Nk must be positive");
@@ -261,8 +263,10 @@ static fhr_status check_nmf(fhr_ctx *ctx, const fhr_nmf_params *p) {
     FHR_ARG(p->ldP % (p->p_dtype == FHR_BF16 ? 8 : 4) == 0, "ldP must be a multiple of 16 bytes");
     FHR_ARG(p->iters >= 0, "iters < 0");
     FHR_ARG(p->K <= p->Nk && (int64_t)p->K <= p->Np, "K > min(Nk, Np)");
-    if (p->init != FHR_INIT_GIVEN && p->init != FHR_INIT_NNDSVD && p->init != FHR_INIT_LEARNED)
+    if (p->init != FHR_INIT_GIVEN && p->init != FHR_INIT_NNDSVD && p->init != FHR_INIT_LEARNED &&
+        p->init != FHR_INIT_CLUSTER)
         return set_error(ctx, FHR_ERR_ARG, "unknown init %d", p->init);
+    if (p->init == FHR_INIT_CLUSTER) FHR_TRY(cluster_check(ctx, p));
     if (p->init == FHR_INIT_LEARNED) {
         FHR_ARG(p->mlp && p->mlp_params, "FHR_INIT_LEARNED needs mlp and mlp_params");
         FHR_ARG(p->mlp->K == p->K && p->mlp->Nk == p->Nk && p->mlp->ldx == p->ldP && p->mlp->x_dtype == p->p_dtype,
@@ -272,20 +276,23 @@ static fhr_status check_nmf(fhr_ctx *ctx, const fhr_nmf_params *p) {
 }
 
 fhr_status nndsvd_ws_size(fhr_ctx *ctx, const fhr_nmf_params *p, size_t *bytes);
+size_t cluster_ws_bytes(const fhr_nmf_params *p);
+fhr_status cluster_run(fhr_ctx *ctx, const fhr_nmf_params *p, const void *P, float *D, void *region);
 size_t mlp_ws_bytes(const fhr_mlp_dims *d, int train);
 fhr_status mlp_forward_impl(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *prm, int64_t M, const void *X, float *Y,
                             void *ws, size_t ws_bytes);
 fhr_status nndsvd_run(fhr_ctx *ctx, const fhr_nmf_params *p, const void *P, float *D, float *W, void *region,
                       int *status);
 
-// Total decomposition workspace: the iteration buffers, then (NNDSVD start
-// only) the initialisation's own region.
+// Total decomposition workspace: the iteration buffers, then the
+// initialisation's own region (NNDSVD, clustering or learned start).
 static fhr_status decompose_ws(fhr_ctx *ctx, const fhr_nmf_params *p, const PassConfig &cfg, void *base, NmfWs *w,
                                size_t *total, void **nn_region) {
     size_t a = carve_nmf(base, p->Np, p->Nk, p->K, cfg.grid, p->iters, w);
     size_t b = 0;
     if (p->init == FHR_INIT_NNDSVD) FHR_TRY(nndsvd_ws_size(ctx, p, &b));
     if (p->init == FHR_INIT_LEARNED) b = mlp_ws_bytes(p->mlp, 0);
+    if (p->init == FHR_INIT_CLUSTER) b = cluster_ws_bytes(p);
     if (nn_region) *nn_region = base ? (void *)((char *)base + a) : nullptr;
     *total = a + b;
     return FHR_OK;
@@ -341,6 +348,17 @@ extern "C" fhr_status fhr_decompose(fhr_ctx *ctx, const fhr_nmf_params *p, const
         FHR_LAUNCHED();
         nmf_d_from_q<<<(unsigned)cdiv(Nk, 128), 128, 0, st>>>(w.Q64, w.GW64, Nk, K, 10, D);
         FHR_LAUNCHED();
+    }
+    if (p->init == FHR_INIT_CLUSTER) {
+        // D0 = k-means centres; W0 = one HALS V half-step from V = 0
+        FHR_TRY(cluster_run(ctx, p, P, D, nn_region));
+        FHR_CUDA(cudaMemsetAsync(W, 0, sizeof(float) * (size_t)p->Np * K, st));
+        nmf_init_given<<<1, 256, 0, st>>>(D, Nk, K, w.D64, &w.state[0]);
+        FHR_LAUNCHED();
+        a.P = P; a.Np = p->Np; a.Nk = Nk; a.ldP = p->ldP; a.D64 = w.D64; a.st = &w.state[0]; a.W = W;
+        a.Qpart = w.Qpart; a.Gpart = w.Gpart; a.ssqpart = w.ssqpart; a.status = w.status;
+        a.mode = PASS_HALS; a.want_ssq = 0;
+        FHR_TRY(launch_pass(ctx, cfg, a));
     }
     nmf_init_given<<<1, 256, 0, st>>>(D, Nk, K, w.D64, &w.state[0]);
     FHR_LAUNCHED();

@@ -30,7 +30,7 @@ template <>
 struct VecF<4> {
     using T = float4;
     __device__ __forceinline__ static float4 ld(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-    __device__ __forceinline__ static float4 ldcg(const float *p) { return __ldcg(reinterpret_cast<const float4 *>(p)); }
+    __device__ __forceinline__ static float4 ldca(const float *p) { return __ldca(reinterpret_cast<const float4 *>(p)); }
     __device__ __forceinline__ static void st(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
     __device__ __forceinline__ static void fma(float4 &a, float w, float4 x) {
         a.x = fmaf(w, x.x, a.x); a.y = fmaf(w, x.y, a.y); a.z = fmaf(w, x.z, a.z); a.w = fmaf(w, x.w, a.w);
@@ -42,10 +42,25 @@ struct VecF<4> {
     }
 };
 template <>
+struct VecF<2> {
+    using T = float2;
+    __device__ __forceinline__ static float2 ld(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+    __device__ __forceinline__ static float2 ldca(const float *p) { return __ldca(reinterpret_cast<const float2 *>(p)); }
+    __device__ __forceinline__ static void st(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+    __device__ __forceinline__ static void fma(float2 &a, float w, float2 x) {
+        a.x = fmaf(w, x.x, a.x); a.y = fmaf(w, x.y, a.y);
+    }
+    __device__ __forceinline__ static float2 zero() { return make_float2(0.f, 0.f); }
+    __device__ __forceinline__ static float get(const float2 &v, int e) { return e == 0 ? v.x : v.y; }
+    __device__ __forceinline__ static void set(float2 &v, int e, float f) {
+        if (e == 0) v.x = f; else v.y = f;
+    }
+};
+template <>
 struct VecF<1> {
     using T = float;
     __device__ __forceinline__ static float ld(const float *p) { return *p; }
-    __device__ __forceinline__ static float ldcg(const float *p) { return __ldcg(p); }
+    __device__ __forceinline__ static float ldca(const float *p) { return __ldca(p); }
     __device__ __forceinline__ static void st(float *p, float v) { *p = v; }
     __device__ __forceinline__ static void fma(float &a, float w, float x) { a = fmaf(w, x, a); }
     __device__ __forceinline__ static float zero() { return 0.f; }
@@ -53,11 +68,13 @@ struct VecF<1> {
     __device__ __forceinline__ static void set(float &v, int, float f) { v = f; }
 };
 
-// Load of a vector the same launch may have written (COH: through L2 only,
-// never a possibly stale L1 line) or of data fixed for the launch.
+// Load of a vector.  COH: the same launch wrote it before a grid-wide
+// barrier (release/acquire fences), so it must be an ordinary coherent load
+// (ld.global.ca), never the read-only non-coherent path the compiler may pick
+// for const restrict pointers.
 template <int VW, bool COH>
 __device__ __forceinline__ typename VecF<VW>::T ldv(const float *p) {
-    if constexpr (COH) return VecF<VW>::ldcg(p);
+    if constexpr (COH) return VecF<VW>::ldca(p);
     else return VecF<VW>::ld(p);
 }
 

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfhr.so")
 
 F32, BF16 = 0, 1
-INIT_GIVEN, INIT_NNDSVD, INIT_LEARNED = 0, 1, 2
+INIT_GIVEN, INIT_NNDSVD, INIT_LEARNED, INIT_CLUSTER = 0, 1, 2, 3
 OK, ERR_ARG, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 
 # Every entry point declared in include/fhr.h (checked by the ABI test).
@@ -37,7 +37,7 @@ class NmfParams(ctypes.Structure):
     _fields_ = [("Np", ctypes.c_int64), ("Nk", ctypes.c_int), ("ldP", ctypes.c_int), ("K", ctypes.c_int),
                 ("iters", ctypes.c_int), ("init", ctypes.c_int), ("p_dtype", ctypes.c_int),
                 ("power_iters", ctypes.c_int), ("seed", ctypes.c_uint64), ("mlp", ctypes.c_void_p),
-                ("mlp_params", ctypes.c_void_p)]
+                ("mlp_params", ctypes.c_void_p), ("kmeans_samples", ctypes.c_int64), ("kmeans_iters", ctypes.c_int)]
 
 
 class Geom(ctypes.Structure):
@@ -216,10 +216,13 @@ class Context:
         return (P, b) if bg is not None else P
 
     # ------------------------------------------------------------ decompose
-    def nmf_params(self, P, Nk, K, iters, init=INIT_GIVEN, power_iters=0, seed=0, mlp=None):
+    def nmf_params(self, P, Nk, K, iters, init=INIT_GIVEN, power_iters=0, seed=0, mlp=None, kmeans_samples=0,
+                   kmeans_iters=0):
         torch = _torch()
         prm = NmfParams(P.shape[0], Nk, P.shape[1], K, iters, init,
                         BF16 if P.dtype == torch.bfloat16 else F32, power_iters, seed)
+        prm.kmeans_samples = kmeans_samples
+        prm.kmeans_iters = kmeans_iters
         if mlp is not None:
             dims, params = mlp
             prm.mlp = ctypes.addressof(dims)
@@ -228,8 +231,9 @@ class Context:
         return prm
 
     def decompose(self, P, Nk, K, iters, *, D=None, W=None, init=None, power_iters=0, seed=0, obj=True,
-                  check_status=True, mlp=None):
-        """Fast-HALS NMF of P (Sec. III).  D [Nk][K], W [Np][K] updated in place (GIVEN) or filled (NNDSVD)."""
+                  check_status=True, mlp=None, kmeans_samples=0, kmeans_iters=0):
+        """Fast-HALS NMF of P (Sec. III).  D [Nk][K], W [Np][K] updated in place (GIVEN) or filled
+        (NNDSVD, CLUSTER, LEARNED)."""
         torch = _torch()
         dev = P.device
         if init is None:
@@ -240,7 +244,7 @@ class Context:
             W = torch.zeros((P.shape[0], K), dtype=torch.float32, device=dev)
         if mlp is not None:
             init = INIT_LEARNED
-        prm = self.nmf_params(P, Nk, K, iters, init, power_iters, seed, mlp)
+        prm = self.nmf_params(P, Nk, K, iters, init, power_iters, seed, mlp, kmeans_samples, kmeans_iters)
         n = ctypes.c_size_t()
         self.check(self.L.fhr_decompose_workspace_size(self._h, ctypes.byref(prm), ctypes.byref(n)))
         ws = self.workspace(n.value)
@@ -420,12 +424,14 @@ class Context:
 
     # ------------------------------------------------------------ pipeline
     def pipeline_params(self, *, Nv, Nr, Nc, Nk, N, K, nmf_iters, mbir_iters, p_dtype=F32, xh_dtype=F32,
-                        host_io=False, power_iters=0, seed=0, angles=None, **mbir_kw):
+                        host_io=False, power_iters=0, seed=0, angles=None, init=INIT_NNDSVD, kmeans_samples=0,
+                        kmeans_iters=0, **mbir_kw):
         mult = 8 if p_dtype == BF16 else 4
         ldP = (Nk + mult - 1) // mult * mult
         prm = PipelineParams()
         prm.norm = NormParams(Nv, Nr, Nc, Nk, ldP, p_dtype)
-        prm.nmf = NmfParams(Nv * Nr * Nc, Nk, ldP, K, nmf_iters, INIT_NNDSVD, p_dtype, power_iters, seed, None, None)
+        prm.nmf = NmfParams(Nv * Nr * Nc, Nk, ldP, K, nmf_iters, init, p_dtype, power_iters, seed, None, None,
+                            kmeans_samples, kmeans_iters)
         prm.geom = self.geom(N, Nr, Nc, Nv, angles)
         mp = self.mbir_params(K, mbir_iters, **mbir_kw)
         prm.mbir = mp
