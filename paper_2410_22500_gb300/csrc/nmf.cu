@@ -317,7 +317,7 @@ extern "C" fhr_status fhr_decompose(fhr_ctx *ctx, const fhr_nmf_params *p, const
     if (!ctx) return FHR_ERR_ARG;
     FHR_TRY(check_nmf(ctx, p));
     FHR_ARG(P && D && W && ws, "null pointer argument");
-    FHR_ARG(aligned(P, 16), "P must be 16-byte aligned");
+    FHR_ARG(aligned(P, 16) && aligned(W, 16), "P and W must be 16-byte aligned");
     FHR_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
     FHR_CUDA(cudaSetDevice(ctx->device));
     PassConfig cfg;

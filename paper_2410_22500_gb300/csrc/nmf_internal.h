@@ -6,7 +6,7 @@
 namespace fhr {
 
 struct PassConfig {
-    int cpt = 0, nt = 0, stages = 0, grid = 0;
+    int cpt = 0, nt = 0, stages = 0, grid = 0, K = 0;
     size_t smem = 0;
     const void *fn = nullptr;
 };

@@ -53,6 +53,7 @@ struct PassArgs {
     int mode;
     int stages;
     int want_ssq;              // accumulate ||P||^2 (first pass only)
+    int K;                     // columns of D / W (set by the launcher)
 };
 
 template <typename TP>

@@ -1,6 +1,9 @@
-// Instantiations and launch dispatch of the fused NMF pass.
-#include "nmf_pass.cuh"
+// Instantiations and launch configuration of the fused NMF pass: the
+// tensor-core kernel (nmf_mma.cuh) up to 1536 (f32) / 2112 (bf16) bins per
+// row, the CUDA-core kernel (nmf_pass.cuh) beyond.
 #include "nmf_internal.h"
+#include "nmf_mma.cuh"
+#include "nmf_pass.cuh"
 
 namespace fhr {
 
@@ -32,6 +35,52 @@ PassFn<__nv_bfloat16> pick<__nv_bfloat16>(int K, int cpt) {
 }
 #undef CASE
 
+template <typename TP>
+static const void *pick_mma(int nkw) {
+    switch (nkw) {
+        case 16: return (const void *)nmf_mma_kernel<TP, 16>;
+        case 32: return (const void *)nmf_mma_kernel<TP, 32>;
+        case 48: return (const void *)nmf_mma_kernel<TP, 48>;
+        case 64: return (const void *)nmf_mma_kernel<TP, 64>;
+        case 80: return (const void *)nmf_mma_kernel<TP, 80>;
+        case 96: return (const void *)nmf_mma_kernel<TP, 96>;
+        case 112: return (const void *)nmf_mma_kernel<TP, 112>;
+        case 128: return (const void *)nmf_mma_kernel<TP, 128>;
+        default: break;
+    }
+    if constexpr (sizeof(TP) == 2) {   // BF16 keeps fewer registers per bin
+        switch (nkw) {
+            case 144: return (const void *)nmf_mma_kernel<TP, 144>;
+            case 160: return (const void *)nmf_mma_kernel<TP, 160>;
+            case 176: return (const void *)nmf_mma_kernel<TP, 176>;
+            default: break;
+        }
+    }
+    return nullptr;
+}
+
+static fhr_status mma_config(fhr_ctx *ctx, int K, int ldP, int p_dtype, PassConfig *cfg) {
+    const int esize = p_dtype == FHR_BF16 ? 2 : 4;
+    const void *fn = p_dtype == FHR_BF16 ? pick_mma<__nv_bfloat16>(mma_nkw(ldP)) : pick_mma<float>(mma_nkw(ldP));
+    if (!fn) return FHR_ERR_UNSUPPORTED;
+    int stages = 8;
+    while (stages > 3 && mma_smem_layout(ldP, esize, stages).total > (size_t)ctx->max_smem_optin) --stages;
+    const size_t smem = mma_smem_layout(ldP, esize, stages).total;
+    if (smem > (size_t)ctx->max_smem_optin) return FHR_ERR_UNSUPPORTED;
+    FHR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FHR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMmaThreads, smem));
+    if (per_sm < 1) return FHR_ERR_UNSUPPORTED;
+    cfg->cpt = 0;
+    cfg->nt = kMmaThreads - 64;
+    cfg->stages = stages;
+    cfg->smem = smem;
+    cfg->grid = ctx->sm_count * per_sm;
+    cfg->fn = fn;
+    cfg->K = K;
+    return FHR_OK;
+}
+
 // Columns per thread: Q for the owned columns stays in registers for the whole
 // launch (cpt * vec * K floats); D is read from shared memory.
 static int max_cpt(int K, int vec) {
@@ -44,6 +93,12 @@ static size_t pass_smem(int K, int NT, int ldP, int esize, int stages) {
 }
 
 fhr_status pass_config(fhr_ctx *ctx, int K, int Nk, int ldP, int p_dtype, PassConfig *cfg) {
+    cfg->K = K;
+    {
+        const fhr_status st = mma_config(ctx, K, ldP, p_dtype, cfg);
+        if (st == FHR_OK) return FHR_OK;
+        if (st != FHR_ERR_UNSUPPORTED) return st;
+    }
     const int vec = p_dtype == FHR_BF16 ? 8 : 4;
     const int esize = p_dtype == FHR_BF16 ? 2 : 4;
     const int ncol = ldP / vec;
@@ -95,6 +150,7 @@ fhr_status pass_config(fhr_ctx *ctx, int K, int Nk, int ldP, int p_dtype, PassCo
 fhr_status launch_pass(fhr_ctx *ctx, const PassConfig &cfg, const PassArgs &a) {
     PassArgs b = a;
     b.stages = cfg.stages;
+    b.K = cfg.K;
     void *args[] = {&b};
     FHR_TIMED(a.mode == PASS_HALS ? TM_NMF_PASS : TM_NNDSVD_PASS,
               cudaLaunchKernel(cfg.fn, dim3(cfg.grid), dim3(cfg.nt + 64), args, cfg.smem, ctx->stream));

@@ -3,22 +3,31 @@
 
 namespace fhr {
 
-__device__ __forceinline__ double footprint_cdf(double s, double hi, double lo) {
-    const double t2 = 0.5 * (hi + lo), t1 = 0.5 * (hi - lo);
-    if (s <= -t2) return 0.0;
-    if (s >= t2) return 1.0;
-    if (s <= -t1) return (s + t2) * (s + t2) / (2.0 * hi * lo);
-    if (s <= t1) return lo / (2.0 * hi) + (s + t1) / hi;
-    return 1.0 - (t2 - s) * (t2 - s) / (2.0 * hi * lo);
+// Cumulative integral of a unit pixel's footprint seen along (cos, sin): a
+// trapezoid of area 1, flat top of height 1/hi for |s| <= (hi - lo)/2, linear to
+// 0 at |s| = (hi + lo)/2 (hi = max(|cos|, |sin|), lo = min).  FP32: the argument
+// is a small offset (|s| < 2) computed in FP64 by the caller.
+__device__ __forceinline__ float footprint_cdf(float s, float hi, float lo) {
+    const float t2 = 0.5f * (hi + lo), t1 = 0.5f * (hi - lo);
+    if (s <= -t2) return 0.f;
+    if (s >= t2) return 1.f;
+    if (s <= -t1) return (s + t2) * (s + t2) / (2.f * hi * lo);
+    if (s <= t1) return lo / (2.f * hi) + (s + t1) / hi;
+    return 1.f - (t2 - s) * (t2 - s) / (2.f * hi * lo);
 }
 
-// area of pixel (px, py) inside the unit strip centred at uc, direction (c, s)
-// not inlined: both tables call the one compiled instance, so equal inputs give equal bits
-__device__ __noinline__ double strip_area(double c, double s, double px, double py, double uc) {
-    const double a = fabs(c), b = fabs(s);
-    const double hi = fmax(a, b), lo = fmin(a, b);
-    const double u0 = px * c + py * s;
-    return footprint_cdf(uc + 0.5 - u0, hi, lo) - footprint_cdf(uc - 0.5 - u0, hi, lo);
+// area of pixel (px, py) inside the unit strip centred at uc, direction (c, s):
+// the pixel's position along the detector in FP64, the footprint integral in FP32.
+// Results below 2^-22 (the rounding level of the FP32 integral) are returned as
+// 0, so a pixel / bin pair that only touches stays exactly 0 in both tables,
+// whichever candidate ranges they scan.  Not inlined: both tables call the one
+// compiled instance, so equal inputs give equal bits.
+__device__ __noinline__ float strip_area(double c, double s, double px, double py, double uc) {
+    const float a = fabsf((float)c), b = fabsf((float)s);
+    const float hi = fmaxf(a, b), lo = fminf(a, b);
+    const float d = (float)(uc - fma(px, c, py * s));
+    const float w = footprint_cdf(d + 0.5f, hi, lo) - footprint_cdf(d - 0.5f, hi, lo);
+    return w < 0x1p-22f ? 0.f : w;
 }
 
 __device__ __forceinline__ void view_dir(const double *angles, int v, int Nv, double *c, double *s) {
@@ -26,12 +35,13 @@ __device__ __forceinline__ void view_dir(const double *angles, int v, int Nv, do
     sincos(th, s, c);
 }
 
-// forward table: one thread per (v, c, line)
+// forward table: one thread per (v, line, c); layout [Nv][N][Nc] so that the
+// rays of one view read consecutive entries for each line
 __global__ void proj_table_fw(const double *angles, int N, int Nc, int Nv, ProjTables t) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)Nv * Nc * N) return;
-    const int l = (int)(idx % N);
-    const int c = (int)((idx / N) % Nc);
+    const int c = (int)(idx % Nc);
+    const int l = (int)((idx / Nc) % N);
     const int v = (int)(idx / ((int64_t)N * Nc));
     double cs, sn;
     view_dir(angles, v, Nv, &cs, &sn);
@@ -57,7 +67,7 @@ __global__ void proj_table_fw(const double *angles, int N, int Nc, int Nv, ProjT
         const int q = s0 + m;
         const double px = rows ? q - h : l - h;
         const double py = rows ? l - h : q - h;
-        w[m] = (float)strip_area(cs, sn, px, py, uc);
+        w[m] = strip_area(cs, sn, px, py, uc);
     }
     t.fw[idx] = make_float4(w[0], w[1], w[2], w[3]);
     t.fws[idx] = s0;
@@ -81,7 +91,7 @@ __global__ void proj_table_bk(const double *angles, int N, int Nc, int Nv, ProjT
     c0 = max(0, min(c0, Nc - 3));
     float w[3];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) w[m] = (float)strip_area(cs, sn, px, py, (c0 + m) - 0.5 * (Nc - 1));
+    for (int m = 0; m < 3; ++m) w[m] = strip_area(cs, sn, px, py, (c0 + m) - 0.5 * (Nc - 1));
     t.bk[idx] = make_float4(w[0], w[1], w[2], (float)c0);
 }
 

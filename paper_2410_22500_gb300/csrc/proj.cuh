@@ -2,13 +2,14 @@
 //
 // A_{(v,c),i} = area(unit pixel i intersect the unit-width strip of bin c at
 // view v).  It is the integral over the bin of the pixel's trapezoidal
-// footprint, so it has a closed form (footprint_cdf below).  The weights are
-// evaluated once per call in double precision into two tables:
-//   forward  [Nv][Nc][N] lines: along the image axis most parallel to the
+// footprint, so it has a closed form (footprint_cdf in proj.cu).  The weights
+// are evaluated once per call (pixel-to-bin offset in FP64, the footprint
+// integral in FP32) into two tables:
+//   forward  [Nv][N][Nc] lines: along the image axis most parallel to the
 //            rays, 4 candidate pixels per line (a strip crosses at most 4),
 //   backward [Nv][N*N]: 3 candidate bins per pixel (a footprint spans <= 3),
-// both rounded to float from the same double, so A^T is the exact transpose
-// of A.  The two gathers apply each weight to a vector of Wl values per
+// both from the one compiled strip_area routine on equal inputs, so A^T is the
+// exact transpose of A.  The two gathers apply each weight to a vector of Wl values per
 // pixel / ray (all slices and subspace channels at once), so every access is
 // a contiguous, vectorised read of Wl floats.
 #pragma once
@@ -18,8 +19,8 @@
 namespace fhr {
 
 struct ProjTables {
-    float4 *fw;        // [Nv][Nc][N] weights of candidates s0..s0+3
-    int *fws;          // [Nv][Nc][N] s0
+    float4 *fw;        // [Nv][N][Nc] weights of candidates s0..s0+3 (per view, line, ray)
+    int *fws;          // [Nv][N][Nc] s0
     uint8_t *rowmaj;   // [Nv] 1: lines are image rows (|cos| >= |sin|)
     float4 *bk;        // [Nv][N*N] {w0, w1, w2, c0}
 };
@@ -84,17 +85,17 @@ template <int VW, bool COH = false>
 __device__ __forceinline__ typename VecF<VW>::T forward_at(const float *__restrict__ x, const ProjTables &t, int N,
                                                            int Nc, int Wl, int item, int ch) {
     using VF = VecF<VW>;
-    const int v = item / Nc;
+    const int v = item / Nc, c = item - v * Nc;
     const bool rows = t.rowmaj[v] != 0;
-    const float4 *fw = t.fw + (size_t)item * N;
-    const int *fs = t.fws + (size_t)item * N;
+    const float4 *fw = t.fw + (size_t)v * N * Nc + c;
+    const int *fs = t.fws + (size_t)v * N * Nc + c;
     const int lstride = rows ? N : 1;     // pixel index = l * lstride + q * qstride
     const int qstride = rows ? 1 : N;
     typename VF::T acc = VF::zero();
     const float *xc = x + ch * VW;
     for (int l = 0; l < N; ++l) {
-        const float4 w = __ldg(fw + l);
-        const int s0 = __ldg(fs + l);
+        const float4 w = __ldg(fw + (size_t)l * Nc);
+        const int s0 = __ldg(fs + (size_t)l * Nc);
         const int p0 = l * lstride + s0 * qstride;
         if (w.x != 0.f) VF::fma(acc, w.x, ldv<VW, COH>(xc + (size_t)p0 * Wl));
         if (w.y != 0.f) VF::fma(acc, w.y, ldv<VW, COH>(xc + (size_t)(p0 + qstride) * Wl));
