@@ -43,7 +43,8 @@ struct MmaSmem {
     uint32_t rs;   // bytes per staged pixel row
 };
 
-__host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stages) {
+// nb: hand-off buffers between phase 1 and phase 3 (pipeline lag + 1)
+__host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stages, int nb) {
     MmaSmem L;
     size_t o = 0;
     auto take = [&](size_t bytes, size_t align) {
@@ -56,15 +57,15 @@ __host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stage
     L.rs = (uint32_t)((cols * esize + 127) / 128 * 128 + 16);
     L.tiles = take((size_t)stages * kMmaRows * L.rs, 128);
     L.wst = take((size_t)stages * kMmaRows * kMaxK * sizeof(float), 128);   // W rows of each staged tile
-    L.wb = take((size_t)2 * 2 * 8 * kMmaWbStride, 128);     // [buffer][big|small or hi|lo][s][48 B]
-    L.red = take((size_t)2 * kMmaCW * 64 * sizeof(float), 16);   // [buffer][warp][s][row]
+    L.wb = take((size_t)nb * 2 * 8 * kMmaWbStride, 128);     // [buffer][big|small or hi|lo][s][48 B]
+    L.red = take((size_t)nb * 64 * 16 * sizeof(float), 16);   // [buffer][s][row][warp, padded to 16]
     // low parts of the D^T fragments: [warp][k-step][lane] x {a0, a2}
     L.dlo = take((size_t)kMmaCW * (mma_nkw(ldP) / (esize == 4 ? 8 : 16)) * 32 * 8, 16);
     L.gsm = take((size_t)kMaxK * kMaxK * sizeof(float), 16);
     L.invd = take((size_t)kMaxK * sizeof(float), 16);
     L.wsc = take((size_t)kMaxK * sizeof(float), 16);
     L.ssq = take((size_t)kMmaCW * sizeof(float), 16);
-    L.bars = take((size_t)(2 * stages + 4) * sizeof(uint64_t), 8);
+    L.bars = take((size_t)(2 * stages + 2 * nb) * sizeof(uint64_t), 8);
     L.total = (o + 127) / 128 * 128;
     return L;
 }
@@ -169,8 +170,11 @@ __host__ __device__ constexpr int mma_tri(int s, int t) {
 __device__ __forceinline__ int mma_perm(int j) { return j < 4 ? 2 * j : 2 * (j - 4) + 1; }
 __device__ __forceinline__ int mma_perm_inv(int r) { return (r & 1) ? 4 + (r >> 1) : (r >> 1); }
 
-template <typename TP, int NKW>
+// LAG: phase 3 of tile i - LAG follows phase 1 of tile i, so the update of a
+// tile has LAG tile periods to complete
+template <typename TP, int NKW, int LAG>
 __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
+    constexpr int NB = LAG + 1;
     constexpr bool F32 = sizeof(TP) == 4;
     constexpr int ES = (int)sizeof(TP);
     constexpr int KS = NKW / MmaK<TP>::STEP;    // GEMM1 k-steps per warp
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const MmaSmem Lyt = mma_smem_layout(a.ldP, ES, S);
+    const MmaSmem Lyt = mma_smem_layout(a.ldP, ES, S, NB);
     const uint32_t sb = smem_u32(smem);
     const uint32_t tiles_a = sb + (uint32_t)Lyt.tiles;
     const uint32_t wb_a = sb + (uint32_t)Lyt.wb;
@@ -201,14 +205,14 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + Lyt.bars);
     uint64_t *empty = full + S;
     uint64_t *redfull = empty + S;
-    uint64_t *wready = redfull + 2;
+    uint64_t *wready = redfull + NB;
     const uint32_t RS = Lyt.rs;
     const uint32_t stage_bytes = kMmaRows * RS;
 
     // zero the ring (row padding must read as finite zeros), the staged w and the partials
     {
         uint4 *z = reinterpret_cast<uint4 *>(smem + Lyt.tiles);
-        const size_t n = (Lyt.red + (size_t)2 * kMmaCW * 64 * sizeof(float) - Lyt.tiles) / 16;
+        const size_t n = (Lyt.red + (size_t)NB * 64 * 16 * sizeof(float) - Lyt.tiles) / 16;
         for (size_t i = tid; i < n; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     if (tid == 0) {
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], NT);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NB; ++i) {
             mbar_init(&redfull[i], NT);
             mbar_init(&wready[i], 1);
         }
@@ -292,10 +296,11 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
         int su = uw % S;
         uint32_t paru = 0;
         for (int64_t i = uw; i < my_tiles; i += 2) {
-            const int b = uw;
+            const int b = (int)(i % NB);
+            const uint32_t hpar = (uint32_t)((i / NB) & 1);
             const int64_t r0 = (blockIdx.x + i * gridDim.x) * kMmaRows;
             const int rows = (int)((a.Np - r0) < kMmaRows ? (a.Np - r0) : kMmaRows);
-            if (!mbar_wait_bounded(&redfull[b], (uint32_t)((i >> 1) & 1)) || !mbar_wait_bounded(&full[su], paru)) {
+            if (!mbar_wait_bounded(&redfull[b], hpar) || !mbar_wait_bounded(&full[su], paru)) {
                 report(a.status, FHR_ERR_TIMEOUT);
                 break;
             }
@@ -319,19 +324,18 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 su -= S;
                 paru ^= 1u;
             }
+            // r[s] for this lane's row: partials of warps 4 grp .. 4 grp + 3 in one
+            // 16-byte load, then the four groups combined by two exchanges
             float r[kMaxK];
 #pragma unroll
             for (int s = 0; s < kMaxK; ++s) {
-                float acc = 0.f;
-                if (s < K)
-                    for (int ww = grp; ww < kMmaCW; ww += 4)
-                        acc += lds_f32(red_a + (uint32_t)(((b * kMmaCW + ww) * 64 + s * 8 + row) * 4));
-                r[s] = acc;
-            }
-#pragma unroll
-            for (int s = 0; s < kMaxK; ++s) {
-                r[s] += __shfl_xor_sync(0xffffffffu, r[s], 1);
-                r[s] += __shfl_xor_sync(0xffffffffu, r[s], 2);
+                r[s] = 0.f;
+                if (s < K) {
+                    const float4 v = lds_f4(red_a + (uint32_t)((((b * 8 + s) * 8 + row) * 16 + 4 * grp) * 4));
+                    r[s] = (v.x + v.y) + (v.z + v.w);
+                    r[s] += __shfl_xor_sync(0xffffffffu, r[s], 1);
+                    r[s] += __shfl_xor_sync(0xffffffffu, r[s], 2);
+                }
             }
             if (a.mode == PASS_HALS) {
                 // Gauss-Seidel over s with u = G w kept current:
@@ -439,16 +443,18 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     float ssq = 0.f;
     float gw[4] = {0.f, 0.f, 0.f, 0.f};   // warp 0: G_W (rows s and s + 8 of the accumulator)
     bool ok = true;
-    int s_cur = 0, s_prev = 0;
+    int s_cur = 0, s3 = 0;            // stages of the tiles in phase 1 and in phase 3
     uint32_t par_cur = 0;
-    int64_t r0_cur = (int64_t)blockIdx.x * kMmaRows, r0_prev = 0;
+    int b1 = 0, b3 = 0;               // hand-off buffers of the tiles in phase 1 and in phase 3
+    uint32_t h1 = 0, h3 = 0;          // and their parities
+    int64_t r0_cur = (int64_t)blockIdx.x * kMmaRows;
     const int64_t rstep = (int64_t)gridDim.x * kMmaRows;
     // ldmatrix row addresses: lane supplies row (lane & 7) of matrix (lane >> 3)
     const uint32_t lrow = (uint32_t)(lane & 7) * RS;
     const int lmat = lane >> 3;
-    for (int64_t i = 0; i <= my_tiles && ok; ++i) {
+    for (int64_t i = 0; i < my_tiles + LAG && ok; ++i) {
         if (i < my_tiles) {
-            const int b = (int)(i & 1);
+            const int b = b1;
             if (!mbar_wait_bounded(&full[s_cur], par_cur)) {
                 ok = false;
                 break;
@@ -497,20 +503,31 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 }
             }
             // partial r: rows s = g (high part) and g + 8 (low part) of the
-            // accumulators, columns 2 tig and 2 tig + 1 (pixel rows)
-            sts_v2f(red_a + (uint32_t)(((b * kMmaCW + warp) * 64 + g * 8 + 2 * tig) * 4),
-                    (acc0[0] + acc0[2]) + (acc1[0] + acc1[2]), (acc0[1] + acc0[3]) + (acc1[1] + acc1[3]));
+            // accumulators, columns 2 tig and 2 tig + 1 (pixel rows) -> red[b][s][row][warp]
+            {
+                const uint32_t ra = red_a + (uint32_t)((((b * 8 + g) * 8 + 2 * tig) * 16 + warp) * 4);
+                sts_f32(ra, (acc0[0] + acc0[2]) + (acc1[0] + acc1[2]));
+                sts_f32(ra + 16 * 4, (acc0[1] + acc0[3]) + (acc1[1] + acc1[3]));
+            }
             mbar_arrive(&redfull[b]);
+            if (++b1 == NB) {
+                b1 = 0;
+                h1 ^= 1u;
+            }
+            r0_cur += rstep;
+            if (++s_cur == S) {
+                s_cur = 0;
+                par_cur ^= 1u;
+            }
         }
-        // ---- phase 3 of the previous tile: Q (k x s) += P^T (k x rows) w (rows x s)
-        if (i >= 1) {
-            const int64_t j = i - 1;
-            const int b = (int)(j & 1);
-            if (!mbar_wait_bounded(&wready[b], (uint32_t)((j >> 1) & 1))) {
+        // ---- phase 3 of tile i - LAG: Q (k x s) += P^T (k x rows) w (rows x s)
+        if (i >= LAG) {
+            const int b = b3;
+            if (!mbar_wait_bounded(&wready[b], h3)) {
                 ok = false;
                 break;
             }
-            const uint32_t tl = tiles_a + (uint32_t)s_prev * stage_bytes;
+            const uint32_t tl = tiles_a + (uint32_t)s3 * stage_bytes;
             const uint32_t wbb = wb_a + (uint32_t)(b * 2 * 8 * kMmaWbStride);
             // w as the k x 8 operand: f32 b0 = w[perm(tig)][g], b1 = w[perm(tig + 4)][g];
             // bf16 b0 = {w[2 tig][g], w[2 tig + 1][g]}, b1 = 0 (rows 8..15)
@@ -542,11 +559,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
             for (int m = 0; m < MB; ++m) {
                 const int m0 = c0 + m * 16;
                 if (F32) {
-                    // A = P^T (16 bins x 8 k): a0 = P[perm(tig)][m0 + g], a1 = P[perm(tig)][m0 + g + 8],
-                    // a2 = P[perm(tig + 4)][m0 + g], a3 = P[perm(tig + 4)][m0 + g + 8]
-                    const uint32_t ra = tl + (uint32_t)mma_perm(tig) * RS + (uint32_t)((m0 + g) * 4);
-                    const uint32_t rb = tl + (uint32_t)mma_perm(tig + 4) * RS + (uint32_t)((m0 + g) * 4);
-                    uint32_t x0 = lds_u32(ra), x1 = lds_u32(ra + 32), x2 = lds_u32(rb), x3 = lds_u32(rb + 32);
+                    // A = P^T (16 bins x 8 k) with MMA row m <-> bin m0 + 2 (m % 8) + m / 8, so that
+                    // a0, a1 (rows g, g + 8) are the adjacent bins m0 + 2g, m0 + 2g + 1 of pixel row
+                    // perm(tig) (one 8-byte load) and a2, a3 the same bins of row perm(tig + 4)
+                    uint32_t x0, x1, x2, x3;
+                    lds_u2(tl + (uint32_t)mma_perm(tig) * RS + (uint32_t)((m0 + 2 * g) * 4), x0, x1);
+                    lds_u2(tl + (uint32_t)mma_perm(tig + 4) * RS + (uint32_t)((m0 + 2 * g) * 4), x2, x3);
                     uint32_t b0_, s0_, b1_, s1_, b2_, s2_, b3_, s3_;
                     tf32_split(x0, b0_, s0_);
                     tf32_split(x1, b1_, s1_);
@@ -564,25 +582,23 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                     mma_bf16(Q[m], a0, a1, a0, a1, wB0, wS0);
                 }
             }
-            mbar_arrive(&empty[s_prev]);
-        }
-        s_prev = s_cur;
-        r0_prev = r0_cur;
-        r0_cur += rstep;
-        if (++s_cur == S) {
-            s_cur = 0;
-            par_cur ^= 1u;
+            mbar_arrive(&empty[s3]);
+            if (++s3 == S) s3 = 0;
+            if (++b3 == NB) {
+                b3 = 0;
+                h3 ^= 1u;
+            }
         }
     }
-    (void)r0_prev;
     if (!ok) report(a.status, FHR_ERR_TIMEOUT);
 
-    // per-CTA partials of Q: c0 = (bin m0 + g, s 2 tig), c1 = (.., 2 tig + 1), c2, c3 = bin + 8
+    // per-CTA partials of Q: c0 = (MMA row g, s 2 tig), c1 = (.., 2 tig + 1), c2, c3 = row g + 8;
+    // MMA row g is bin m0 + g (bf16) or m0 + 2g (f32), row g + 8 bin m0 + g + 8 or m0 + 2g + 1
 #pragma unroll
     for (int m = 0; m < MB; ++m) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const int k = c0 + m * 16 + g + (e >> 1) * 8;
+            const int k = c0 + m * 16 + (F32 ? 2 * g + (e >> 1) : g + (e >> 1) * 8);
             const int s = 2 * tig + (e & 1);
             if (k < a.Nk && s < K) a.Qpart[((size_t)blockIdx.x * a.Nk + k) * K + s] = Q[m][e];
         }

@@ -35,24 +35,32 @@ PassFn<__nv_bfloat16> pick<__nv_bfloat16>(int K, int cpt) {
 }
 #undef CASE
 
+// pipeline lag of the tensor-core pass per element type (bf16 tiles are half
+// the size, so the ring has room for the deeper hand-off)
+template <typename TP>
+struct MmaLag {
+    static constexpr int V = sizeof(TP) == 2 ? 2 : 1;
+};
+
 template <typename TP>
 static const void *pick_mma(int nkw) {
+    constexpr int L = MmaLag<TP>::V;
     switch (nkw) {
-        case 16: return (const void *)nmf_mma_kernel<TP, 16>;
-        case 32: return (const void *)nmf_mma_kernel<TP, 32>;
-        case 48: return (const void *)nmf_mma_kernel<TP, 48>;
-        case 64: return (const void *)nmf_mma_kernel<TP, 64>;
-        case 80: return (const void *)nmf_mma_kernel<TP, 80>;
-        case 96: return (const void *)nmf_mma_kernel<TP, 96>;
-        case 112: return (const void *)nmf_mma_kernel<TP, 112>;
-        case 128: return (const void *)nmf_mma_kernel<TP, 128>;
+        case 16: return (const void *)nmf_mma_kernel<TP, 16, L>;
+        case 32: return (const void *)nmf_mma_kernel<TP, 32, L>;
+        case 48: return (const void *)nmf_mma_kernel<TP, 48, L>;
+        case 64: return (const void *)nmf_mma_kernel<TP, 64, L>;
+        case 80: return (const void *)nmf_mma_kernel<TP, 80, L>;
+        case 96: return (const void *)nmf_mma_kernel<TP, 96, L>;
+        case 112: return (const void *)nmf_mma_kernel<TP, 112, L>;
+        case 128: return (const void *)nmf_mma_kernel<TP, 128, L>;
         default: break;
     }
     if constexpr (sizeof(TP) == 2) {   // BF16 keeps fewer registers per bin
         switch (nkw) {
-            case 144: return (const void *)nmf_mma_kernel<TP, 144>;
-            case 160: return (const void *)nmf_mma_kernel<TP, 160>;
-            case 176: return (const void *)nmf_mma_kernel<TP, 176>;
+            case 144: return (const void *)nmf_mma_kernel<TP, 144, L>;
+            case 160: return (const void *)nmf_mma_kernel<TP, 160, L>;
+            case 176: return (const void *)nmf_mma_kernel<TP, 176, L>;
             default: break;
         }
     }
@@ -63,9 +71,10 @@ static fhr_status mma_config(fhr_ctx *ctx, int K, int ldP, int p_dtype, PassConf
     const int esize = p_dtype == FHR_BF16 ? 2 : 4;
     const void *fn = p_dtype == FHR_BF16 ? pick_mma<__nv_bfloat16>(mma_nkw(ldP)) : pick_mma<float>(mma_nkw(ldP));
     if (!fn) return FHR_ERR_UNSUPPORTED;
+    const int nb = (p_dtype == FHR_BF16 ? MmaLag<__nv_bfloat16>::V : MmaLag<float>::V) + 1;
     int stages = 8;
-    while (stages > 3 && mma_smem_layout(ldP, esize, stages).total > (size_t)ctx->max_smem_optin) --stages;
-    const size_t smem = mma_smem_layout(ldP, esize, stages).total;
+    while (stages > nb + 1 && mma_smem_layout(ldP, esize, stages, nb).total > (size_t)ctx->max_smem_optin) --stages;
+    const size_t smem = mma_smem_layout(ldP, esize, stages, nb).total;
     if (smem > (size_t)ctx->max_smem_optin) return FHR_ERR_UNSUPPORTED;
     FHR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
