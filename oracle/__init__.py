@@ -15,6 +15,8 @@ Every function cites the passage of the paper it follows.  Parity status:
   expansion        pinned (identity dictionary, commutes with the projector)
   MLP warm start   pinned (closed-form activations, layer-wise numpy, central
                    differences of the loss, AdamW closed form)
+  FBP variant      pinned (textbook ramp samples, filter = direct convolution
+                   with the kernel, disk reconstruction from analytic chords)
   clustering start pinned (published splitmix64 outputs, separated clusters
                    converge to their label means, monotone Lloyd cost, K = 1
                    mean, zero-distance samples never seeded, K = 1 V step)
@@ -82,6 +84,10 @@ def lib():
             L.or_mbir.argtypes = [ctypes.c_int] * 5 + [_dp, _dp, _dp, _dp, ctypes.POINTER(_MbirParams), _dp, _dp]
             L.or_mbir_sigmas.argtypes = [ctypes.c_long, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_int, _dp, _dp]
             L.or_expand.argtypes = [ctypes.c_int] * 4 + [_dp, _dp, _dp]
+            L.or_ramp.restype = ctypes.c_double
+            L.or_ramp.argtypes = [ctypes.c_int]
+            L.or_ramp_filter.argtypes = [ctypes.c_int] * 3 + [_dp, _dp]
+            L.or_fbp.argtypes = [ctypes.c_int] * 3 + [_dp, ctypes.c_int, _dp, _dp]
             vp = ctypes.c_void_p
             L.or_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_int, vp]
             L.or_splitmix64.restype = None
@@ -279,6 +285,34 @@ def backproject(y, N, theta):
     theta = _f64(theta)
     x = np.empty((N, N, Wl))
     lib().or_backproject(N, Nc, Nv, _d(theta), Wl, _d(y), _d(x))
+    return x
+
+
+def ramp(n):
+    """The sampled ramp filter h[n] of the FBP variant (Kak and Slaney, tau = 1)."""
+    return lib().or_ramp(int(n))
+
+
+def ramp_filter(p):
+    """q[v][c] = sum_c' h[c - c'] p[v][c'] along the detector, p [Nv][Nc][Wl]."""
+    p = _f64(p)
+    Nv, Nc = p.shape[:2]
+    Wl = p.shape[2] if p.ndim == 3 else 1
+    q = np.empty((Nv, Nc, Wl))
+    lib().or_ramp_filter(Nv, Nc, Wl, _d(p), _d(q))
+    return q
+
+
+def fbp(p, N, theta):
+    """Filtered back-projection x = (pi / Nv) A^T (h * p): p [Nv][Nc][Wl] -> x [N][N][Wl]."""
+    p = _f64(p)
+    Nv, Nc = p.shape[:2]
+    Wl = p.shape[2] if p.ndim == 3 else 1
+    theta = _f64(theta)
+    x = np.empty((N, N, Wl))
+    rc = lib().or_fbp(N, Nc, Nv, _d(theta), Wl, _d(p), _d(x))
+    if rc:
+        raise ValueError("or_fbp failed: %d" % rc)
     return x
 
 

@@ -488,6 +488,51 @@ void or_backproject(int N, int Nc, int Nv, const double *theta, int Wl, const do
 }
 
 /* ------------------------------------------------------------------------
+ * Filtered back-projection of the subspace sinograms (the "FHR with FBP"
+ * variant, Sec. V / Table II), the paper's faster alternative to MBIR.
+ * Reading (the paper names FBP without its discretisation): the textbook
+ * parallel-beam FBP with the band-limited ramp (Ram-Lak) filter sampled at the
+ * bin spacing tau = 1 (Kak and Slaney, Sec. 3.3.3):
+ *   h[0] = 1 / (4 tau^2), h[n] = 0 for even n != 0, h[n] = -1 / (n pi tau)^2 odd;
+ *   q[v][c] = tau * sum_c' h[c - c'] p[v][c'] (linear convolution, zero outside
+ *   the detector);
+ *   x = (pi / Nv) A^T q, with A^T the strip-area back-projector above.
+ * ---------------------------------------------------------------------- */
+double or_ramp(int n)
+{
+    if (n == 0) return 0.25;
+    if (n % 2 == 0) return 0.0;
+    return -1.0 / ((double)n * (double)n * M_PI * M_PI);
+}
+
+void or_ramp_filter(int Nv, int Nc, int Wl, const double *p, double *q)
+{
+    for (int v = 0; v < Nv; ++v)
+        for (int c = 0; c < Nc; ++c) {
+            double *qo = q + ((size_t)v * Nc + c) * Wl;
+            for (int w = 0; w < Wl; ++w) qo[w] = 0.0;
+            for (int c2 = 0; c2 < Nc; ++c2) {
+                double h = or_ramp(c - c2);
+                if (h == 0.0) continue;
+                const double *pi = p + ((size_t)v * Nc + c2) * Wl;
+                for (int w = 0; w < Wl; ++w) qo[w] += h * pi[w];
+            }
+        }
+}
+
+int or_fbp(int N, int Nc, int Nv, const double *theta, int Wl, const double *p, double *x)
+{
+    double *q = (double *)malloc(sizeof(double) * (size_t)Nv * Nc * Wl);
+    if (!q) return OR_ERR_NOMEM;
+    or_ramp_filter(Nv, Nc, Wl, p, q);
+    or_backproject(N, Nc, Nv, theta, Wl, q, x);
+    const double sc = M_PI / (double)Nv;
+    for (size_t i = 0; i < (size_t)N * N * Wl; ++i) x[i] *= sc;
+    free(q);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------
  * MBIR reconstruction of each subspace channel, Eq. (recon):
  *   x_j = argmin_x  1/(2 sigma_v^2) ||V_j - A x||^2 + h(x),
  * with the qGGMRF prior h (Sec. III; the paper gives no formula, it cites the
