@@ -291,7 +291,7 @@ def run_ours(args, rank, world, device):
         "e2e": {"value": world * vb / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": "nmf_pass (fused fast-HALS pass)", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": "nmf_mma_kernel (fused fast-HALS pass, warp MMA)", "achieved": achieved,
                      "peak": peak, "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
                      if peak_kind == "measured" else "fallback", "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,

@@ -148,6 +148,9 @@ fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *prm,
 #define FHR_INIT_LEARNED 2
 #define FHR_INIT_CLUSTER 3
 
+#define FHR_RECON_MBIR 0
+#define FHR_RECON_FBP 1
+
 struct fhr_mlp_dims_s;
 
 typedef struct {
@@ -244,6 +247,21 @@ fhr_status fhr_reconstruct_workspace_size(fhr_ctx *ctx, const fhr_geom *g, const
                                           size_t *bytes);
 fhr_status fhr_reconstruct(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_params *prm,
                            const float *sino, float *xs, void *ws, size_t ws_bytes);
+
+/* ------------------------------------------------------------------------
+ * Filtered back-projection: the paper's faster reconstruction variant
+ * ("FHR with FBP", Sec. V, Table II), in place of the MBIR of Eq. (recon).
+ * Textbook parallel-beam FBP (the paper gives no discretisation): the
+ * band-limited ramp filter sampled at the unit bin spacing,
+ *   h[0] = 1/4, h[n] = -1/(pi n)^2 for odd n, 0 for even n != 0,
+ * applied along the detector as a linear convolution (zero outside), then
+ * x = (pi / Nv) A^T q with the strip-area back-projector of fhr_backproject.
+ *   sino [Nv][Nc][Wl] -> xs [N][N][Wl] (Wl = Nr*K values per ray / pixel;
+ *   xs 16-byte aligned when Wl % 4 == 0).  Nc <= 1024.
+ * ---------------------------------------------------------------------- */
+fhr_status fhr_fbp_workspace_size(fhr_ctx *ctx, const fhr_geom *geom, int Wl, size_t *bytes);
+fhr_status fhr_fbp(fhr_ctx *ctx, const fhr_geom *geom, int Wl, const float *sino, float *xs,
+                   void *ws, size_t ws_bytes);
 
 /* ------------------------------------------------------------------------
  * Batched MBIR: Eq. (recon) for every channel and slice of nprob independent
@@ -347,6 +365,7 @@ typedef struct {
     fhr_mbir_params mbir;
     int xh_dtype;
     int host_io;
+    int recon;   /* FHR_RECON_MBIR (Eq. recon, default) or FHR_RECON_FBP (fhr_fbp) */
 } fhr_pipeline_params;
 
 fhr_status fhr_pipeline_workspace_size(fhr_ctx *ctx, const fhr_pipeline_params *prm, size_t *bytes);

@@ -376,8 +376,8 @@ def expand(xs, D, N, Nr):
 
 # ---------------------------------------------------------------- pipeline
 def fhr_pipeline(y, y0, K, N, theta, *, nmf_iters=200, mbir_iters=20, dead=None, bg=None,
-                 init=None, p=1.2, T=1.0, snr_db=30.0, momentum=False):
-    """Algorithm 1 end to end: normalise -> NMF -> MBIR per channel -> expansion.
+                 init=None, p=1.2, T=1.0, snr_db=30.0, momentum=False, recon="mbir"):
+    """Algorithm 1 end to end: normalise -> NMF -> MBIR (or FBP) per channel -> expansion.
 
     init: None for NNDSVD, else a (D0, W0) pair.  Returns a dict of every
     intermediate (P, D, W, obj, xs, xh, sigmas)."""
@@ -387,7 +387,10 @@ def fhr_pipeline(y, y0, K, N, theta, *, nmf_iters=200, mbir_iters=20, dead=None,
     D, W, obj = nmf(P, D0, W0, nmf_iters)
     V = W.reshape(Nv, Nc, Nr * K)
     sv, sx = mbir_sigmas(W, K, Nc, snr_db)
-    xs = mbir(V, N, Nr, K, theta, sv, sx, p=p, T=T, iters=mbir_iters, momentum=momentum)
+    if recon == "fbp":
+        xs = fbp(V, N, theta)
+    else:
+        xs = mbir(V, N, Nr, K, theta, sv, sx, p=p, T=T, iters=mbir_iters, momentum=momentum)
     xh = expand(xs, D, N, Nr)
     return dict(P=P, D0=D0, W0=W0, D=D, W=W, obj=obj, sv=sv, sx=sx, xs=xs, xh=xh)
 

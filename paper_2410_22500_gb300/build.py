@@ -83,7 +83,7 @@ if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))
 
 
-KERNEL_SOURCES = {"nmf_pass": ["nmf_pass.cuh", "nmf_pass_inst.cu", "common.cuh"]}
+KERNEL_SOURCES = {"nmf_pass": ["nmf_mma.cuh", "nmf_pass.cuh", "nmf_pass_inst.cu", "nmf_internal.h", "common.cuh"]}
 
 
 def kernel_digest(name: str) -> str:

@@ -58,7 +58,7 @@ __host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stage
     L.tiles = take((size_t)stages * kMmaRows * L.rs, 128);
     L.wst = take((size_t)stages * kMmaRows * kMaxK * sizeof(float), 128);   // W rows of each staged tile
     L.wb = take((size_t)nb * 2 * 8 * kMmaWbStride, 128);     // [buffer][big|small or hi|lo][s][48 B]
-    L.red = take((size_t)nb * 64 * 16 * sizeof(float), 16);   // [buffer][s][row][warp, padded to 16]
+    L.red = take((size_t)nb * 16 * 64 * sizeof(float), 16);   // [buffer][warp, padded to 16][row][s]
     // low parts of the D^T fragments: [warp][k-step][lane] x {a0, a2}
     L.dlo = take((size_t)kMmaCW * (mma_nkw(ldP) / (esize == 4 ? 8 : 16)) * 32 * 8, 16);
     L.gsm = take((size_t)kMaxK * kMaxK * sizeof(float), 16);
@@ -324,15 +324,21 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 su -= S;
                 paru ^= 1u;
             }
-            // r[s] for this lane's row: partials of warps 4 grp .. 4 grp + 3 in one
-            // 16-byte load, then the four groups combined by two exchanges
+            // r[s] for this lane's row: the partials of warps 4 grp .. 4 grp + 3 (two
+            // 16-byte loads each: s 0..3, 4..7), then the four groups combined by two exchanges
             float r[kMaxK];
 #pragma unroll
+            for (int s = 0; s < kMaxK; ++s) r[s] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t ra = red_a + (uint32_t)(((b * 16 + 4 * grp + j) * 64 + row * 8) * 4);
+                const float4 v0 = lds_f4(ra), v1 = lds_f4(ra + 16);
+                r[0] += v0.x; r[1] += v0.y; r[2] += v0.z; r[3] += v0.w;
+                r[4] += v1.x; r[5] += v1.y; r[6] += v1.z; r[7] += v1.w;
+            }
+#pragma unroll
             for (int s = 0; s < kMaxK; ++s) {
-                r[s] = 0.f;
                 if (s < K) {
-                    const float4 v = lds_f4(red_a + (uint32_t)((((b * 8 + s) * 8 + row) * 16 + 4 * grp) * 4));
-                    r[s] = (v.x + v.y) + (v.z + v.w);
                     r[s] += __shfl_xor_sync(0xffffffffu, r[s], 1);
                     r[s] += __shfl_xor_sync(0xffffffffu, r[s], 2);
                 }
@@ -503,11 +509,11 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 }
             }
             // partial r: rows s = g (high part) and g + 8 (low part) of the
-            // accumulators, columns 2 tig and 2 tig + 1 (pixel rows) -> red[b][s][row][warp]
+            // accumulators, columns 2 tig and 2 tig + 1 (pixel rows) -> red[b][warp][row][s]
             {
-                const uint32_t ra = red_a + (uint32_t)((((b * 8 + g) * 8 + 2 * tig) * 16 + warp) * 4);
+                const uint32_t ra = red_a + (uint32_t)(((b * 16 + warp) * 64 + 2 * tig * 8 + g) * 4);
                 sts_f32(ra, (acc0[0] + acc0[2]) + (acc1[0] + acc1[2]));
-                sts_f32(ra + 16 * 4, (acc0[1] + acc0[3]) + (acc1[1] + acc1[3]));
+                sts_f32(ra + 8 * 4, (acc0[1] + acc0[3]) + (acc1[1] + acc1[3]));
             }
             mbar_arrive(&redfull[b]);
             if (++b1 == NB) {

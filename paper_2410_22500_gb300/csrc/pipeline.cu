@@ -6,6 +6,9 @@ namespace fhr {
 fhr_status reconstruct_impl(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_params *p, const float *sino, float *xs,
                             void *ws, size_t ws_bytes);
 size_t reconstruct_ws_bytes(const fhr_geom *g, int K);
+fhr_status fbp_impl(fhr_ctx *ctx, const fhr_geom *g, int Wl, const float *sino, float *xs, void *ws,
+                    size_t ws_bytes);
+size_t fbp_ws_bytes(const fhr_geom *g, int Wl);
 fhr_status expand_impl(fhr_ctx *ctx, int N, int Nr, int K, int Nk, int k0, int k1, const float *xs, const float *D,
                        int dt, void *xh);
 
@@ -37,6 +40,7 @@ static fhr_status pipe_check(fhr_ctx *ctx, const fhr_pipeline_params *p) {
     FHR_ARG(p->nmf.init == FHR_INIT_NNDSVD || p->nmf.init == FHR_INIT_CLUSTER,
             "the pipeline starts the decomposition from NNDSVD or the clustering start");
     FHR_ARG(p->xh_dtype == FHR_F32 || p->xh_dtype == FHR_BF16, "bad xh_dtype");
+    FHR_ARG(p->recon == FHR_RECON_MBIR || p->recon == FHR_RECON_FBP, "bad recon");
     return FHR_OK;
 }
 
@@ -57,7 +61,8 @@ static fhr_status pipe_carve(fhr_ctx *ctx, const fhr_pipeline_params *p, void *b
     t.xs = c.take<float>((size_t)p->geom.N * p->geom.N * n.Nr * K);
     FHR_TRY(fhr_decompose_workspace_size(ctx, &p->nmf, &t.nmf_bytes));
     t.nmf_ws = c.take<char>(t.nmf_bytes);
-    t.mbir_bytes = reconstruct_ws_bytes(&p->geom, K);
+    t.mbir_bytes = p->recon == FHR_RECON_FBP ? fbp_ws_bytes(&p->geom, p->geom.Nr * K)
+                                             : reconstruct_ws_bytes(&p->geom, K);
     t.mbir_ws = c.take<char>(t.mbir_bytes);
     if (w) *w = t;
     *total = c.size();
@@ -104,7 +109,10 @@ extern "C" fhr_status fhr_pipeline(fhr_ctx *ctx, const fhr_pipeline_params *p, c
     FHR_TRY(fhr_decompose(ctx, &p->nmf, w.P, D_out, w.W, obj, w.nmf_ws, w.nmf_bytes));
     const size_t nxs = (size_t)p->geom.N * p->geom.N * n.Nr * K;
     FHR_CUDA(cudaMemsetAsync(w.xs, 0, nxs * sizeof(float), st));
-    FHR_TRY(reconstruct_impl(ctx, &p->geom, &p->mbir, w.W, w.xs, w.mbir_ws, w.mbir_bytes));
+    if (p->recon == FHR_RECON_FBP)
+        FHR_TRY(fbp_impl(ctx, &p->geom, n.Nr * K, w.W, w.xs, w.mbir_ws, w.mbir_bytes));
+    else
+        FHR_TRY(reconstruct_impl(ctx, &p->geom, &p->mbir, w.W, w.xs, w.mbir_ws, w.mbir_bytes));
     void *xo = p->host_io ? w.xh : xh;
     FHR_TRY(expand_impl(ctx, p->geom.N, n.Nr, K, n.Nk, 0, 0, w.xs, D_out, p->xh_dtype, xo));
     gather_status<<<1, 32, 0, st>>>(w.status, (const int *)w.nmf_ws, (const int *)w.mbir_ws);

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libfhr.so")
 
 F32, BF16 = 0, 1
 INIT_GIVEN, INIT_NNDSVD, INIT_LEARNED, INIT_CLUSTER = 0, 1, 2, 3
+RECON_MBIR, RECON_FBP = 0, 1
 OK, ERR_ARG, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 
 # Every entry point declared in include/fhr.h (checked by the ABI test).
@@ -25,6 +26,7 @@ ENTRY_POINTS = (
     "fhr_pipeline_workspace_size", "fhr_pipeline", "fhr_profile_enable", "fhr_profile_read",
     "fhr_decompose_static", "fhr_mlp_workspace_size", "fhr_mlp_forward", "fhr_mlp_grad", "fhr_mlp_adamw",
     "fhr_reconstruct_batch_workspace_size", "fhr_reconstruct_batch", "fhr_reconstruct_batch_autotune",
+    "fhr_fbp_workspace_size", "fhr_fbp",
 )
 
 
@@ -75,7 +77,7 @@ def mlp_nparams(Nk, H1, H2, K):
 
 class PipelineParams(ctypes.Structure):
     _fields_ = [("norm", NormParams), ("nmf", NmfParams), ("geom", Geom), ("mbir", MbirParams),
-                ("xh_dtype", ctypes.c_int), ("host_io", ctypes.c_int)]
+                ("xh_dtype", ctypes.c_int), ("host_io", ctypes.c_int), ("recon", ctypes.c_int)]
 
 
 _lib = None
@@ -123,6 +125,8 @@ def load():
         L.fhr_reconstruct_batch_workspace_size.argtypes = [vp, ctypes.c_int, PP, BP, szp]
         L.fhr_reconstruct_batch.argtypes = [vp, ctypes.c_int, PP, BP, vp, sz]
         L.fhr_reconstruct_batch_autotune.argtypes = [vp, ctypes.c_int, PP, BP, vp, sz, ctypes.POINTER(ctypes.c_int)]
+        L.fhr_fbp_workspace_size.argtypes = [vp, ctypes.POINTER(Geom), ctypes.c_int, szp]
+        L.fhr_fbp.argtypes = [vp, ctypes.POINTER(Geom), ctypes.c_int, vp, vp, vp, sz]
         L.fhr_profile_enable.argtypes = [vp, ctypes.c_int]
         L.fhr_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong),
                                        ctypes.POINTER(ctypes.c_double)]
@@ -320,6 +324,20 @@ class Context:
             self.check(self.status(ws))
         return xs
 
+    # ------------------------------------------------------------ FBP variant
+    def fbp(self, sino, N, *, angles=None, xs=None):
+        """Filtered back-projection: sino [Nv][Nc][Wl] -> xs [N][N][Wl]."""
+        torch = _torch()
+        Nv, Nc, Wl = sino.shape
+        g = self.geom(N, 1, Nc, Nv, angles)
+        n = ctypes.c_size_t()
+        self.check(self.L.fhr_fbp_workspace_size(self._h, ctypes.byref(g), Wl, ctypes.byref(n)))
+        ws = self.workspace(n.value)
+        if xs is None:
+            xs = torch.empty((N, N, Wl), dtype=torch.float32, device=sino.device)
+        self.check(self.L.fhr_fbp(self._h, ctypes.byref(g), Wl, _ptr(sino), _ptr(xs), _ptr(ws), n.value))
+        return xs
+
     # ------------------------------------------------------------ batched MBIR
     @staticmethod
     def batch_problems(sinos, Ns, Ks, xss, *, Nr=1, angles=None, sigmas=None):
@@ -425,7 +443,7 @@ class Context:
     # ------------------------------------------------------------ pipeline
     def pipeline_params(self, *, Nv, Nr, Nc, Nk, N, K, nmf_iters, mbir_iters, p_dtype=F32, xh_dtype=F32,
                         host_io=False, power_iters=0, seed=0, angles=None, init=INIT_NNDSVD, kmeans_samples=0,
-                        kmeans_iters=0, **mbir_kw):
+                        kmeans_iters=0, recon=RECON_MBIR, **mbir_kw):
         mult = 8 if p_dtype == BF16 else 4
         ldP = (Nk + mult - 1) // mult * mult
         prm = PipelineParams()
@@ -438,6 +456,7 @@ class Context:
         prm._keep = mp._keep
         prm.xh_dtype = xh_dtype
         prm.host_io = int(host_io)
+        prm.recon = recon
         return prm
 
     def pipeline_workspace(self, prm):

@@ -59,7 +59,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu\n", offsetof(fhr_nmf_params, seed), offsetof(fhr_mbir_params, sigma_v),
          offsetof(fhr_pipeline_params, geom), offsetof(fhr_pipeline_params, mbir),
          offsetof(fhr_pipeline_params, host_io), offsetof(fhr_nmf_params, mlp_params), sizeof(fhr_mlp_dims));
-  printf("%zu %zu\n", offsetof(fhr_nmf_params, kmeans_samples), offsetof(fhr_nmf_params, kmeans_iters));
+  printf("%zu %zu %zu\n", offsetof(fhr_nmf_params, kmeans_samples), offsetof(fhr_nmf_params, kmeans_iters),
+         offsetof(fhr_pipeline_params, recon));
   printf("%zu %zu %zu %zu %zu\n", sizeof(fhr_problem), offsetof(fhr_problem, sino), offsetof(fhr_problem, sigma_x),
          sizeof(fhr_batch_params), offsetof(fhr_batch_params, tile));
   return 0;
@@ -74,7 +75,8 @@ int main(void) {
     assert offs == [fhr.NmfParams.seed.offset, fhr.MbirParams.sigma_v.offset, fhr.PipelineParams.geom.offset,
                     fhr.PipelineParams.mbir.offset, fhr.PipelineParams.host_io.offset, fhr.NmfParams.mlp_params.offset,
                     ctypes.sizeof(fhr.MlpDims)]
-    assert km == [fhr.NmfParams.kmeans_samples.offset, fhr.NmfParams.kmeans_iters.offset]
+    assert km == [fhr.NmfParams.kmeans_samples.offset, fhr.NmfParams.kmeans_iters.offset,
+                  fhr.PipelineParams.recon.offset]
     assert batch == [ctypes.sizeof(fhr.Problem), fhr.Problem.sino.offset, fhr.Problem.sigma_x.offset,
                      ctypes.sizeof(fhr.BatchParams), fhr.BatchParams.tile.offset]
 
