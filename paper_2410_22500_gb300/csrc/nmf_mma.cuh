@@ -59,8 +59,8 @@ __host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stage
     L.wst = take((size_t)stages * kMmaRows * kMaxK * sizeof(float), 128);   // W rows of each staged tile
     L.wb = take((size_t)nb * 2 * 8 * kMmaWbStride, 128);     // [buffer][big|small or hi|lo][s][48 B]
     L.red = take((size_t)nb * 16 * 64 * sizeof(float), 16);   // [buffer][warp, padded to 16][row][s]
-    // low parts of the D^T fragments: [warp][k-step][lane] x {a0, a2}
-    L.dlo = take((size_t)kMmaCW * (mma_nkw(ldP) / (esize == 4 ? 8 : 16)) * 32 * 8, 16);
+    // f32: low parts of the D^T fragments, [warp][k-step][lane] x {a0, a2} (bf16 keeps them in registers)
+    L.dlo = take(esize == 4 ? (size_t)kMmaCW * (mma_nkw(ldP) / 8) * 32 * 8 : 0, 16);
     L.gsm = take((size_t)kMaxK * kMaxK * sizeof(float), 16);
     L.invd = take((size_t)kMaxK * sizeof(float), 16);
     L.wsc = take((size_t)kMaxK * sizeof(float), 16);
@@ -182,9 +182,14 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     constexpr int NT = kMmaCW * 32;             // consumer threads
 
     const int tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
+    const int hw = tid >> 5, lane = tid & 31;   // hardware warp index
     const int g = lane >> 2, tig = lane & 3;
     const int K = a.K;
+    // roles: warps 1 and 5 update, warp 9 produces (warps w and w + 4k share an SM
+    // sub-partition, so the latency-bound update warps share theirs with one
+    // consumer and the mostly idle producer); the other 13 warps are consumers 0..12
+    const int role = (hw == 1 || hw == 5) ? 1 : (hw == 9 ? 2 : 0);
+    const int warp = role == 0 ? hw - (hw > 1) - (hw > 5) - (hw > 9) : (role == 1 ? (hw == 5) : 0);
     const int S = a.stages;
     const int64_t ntiles = (a.Np + kMmaRows - 1) / kMmaRows;
     const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -233,7 +238,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     }
     __syncthreads();
 
-    if (warp == kMmaCW + 2) {
+    if (role == 2) {
         // ---------------- producer warp: one bulk copy per pixel row
         if (lane == 0) {
             int s = 0;
@@ -273,10 +278,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
         return;
     }
 
-    if (warp >= kMmaCW) {
+    if (role == 1) {
         // ---------------- update warps: warp u takes the tiles i with i % 2 == u;
         // lane = (row, group of 4 partial sums)
-        const int uw = warp - kMmaCW;
+        const int uw = warp;   // 0 or 1
         const int row = lane >> 2, grp = lane & 3;
         // G (constant for the launch): upper triangle in registers
         float gu[kMaxK * (kMaxK + 1) / 2];
@@ -300,7 +305,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
             const uint32_t hpar = (uint32_t)((i / NB) & 1);
             const int64_t r0 = (blockIdx.x + i * gridDim.x) * kMmaRows;
             const int rows = (int)((a.Np - r0) < kMmaRows ? (a.Np - r0) : kMmaRows);
-            if (!mbar_wait_bounded(&redfull[b], hpar) || !mbar_wait_bounded(&full[su], paru)) {
+            // the tile's W rows arrive with its data: read them before waiting for phase 1
+            if (!mbar_wait_bounded(&full[su], paru)) {
                 report(a.status, FHR_ERR_TIMEOUT);
                 break;
             }
@@ -318,6 +324,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                     for (int s = 0; s < kMaxK; ++s)
                         if (s < K) w[s] = a.W[(r0 + row) * K + s] * sc[s];
                 }
+            }
+            if (!mbar_wait_bounded(&redfull[b], hpar)) {
+                report(a.status, FHR_ERR_TIMEOUT);
+                break;
             }
             su += 2;
             if (su >= S) {
@@ -418,6 +428,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     // D^T fragments, the 16 x k operand of phase 1: rows 0..7 the high parts
     // (registers), rows 8..15 the low parts (shared memory), [k-step][a0/a1, a2/a3]
     uint32_t da[KS][2];   // f32: big; bf16: hi
+    // bf16 keeps the low parts in registers too (fewer registers per bin than f32)
+    constexpr bool DL_REG = !F32;
+    uint32_t dlr[DL_REG ? KS : 1][2];
 #pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
 #pragma unroll
@@ -437,7 +450,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 const float h0 = __bfloat162float(__float2bfloat16_rn(v0));
                 const float h1 = __bfloat162float(__float2bfloat16_rn(v1));
                 da[ks][h] = pack_bf16(v0, v1);
-                sts_u32(dlo_a + (uint32_t)(((warp * KS + ks) * 32 + lane) * 8 + 4 * h), pack_bf16(v0 - h0, v1 - h1));
+                if constexpr (DL_REG) dlr[ks][h] = pack_bf16(v0 - h0, v1 - h1);
+                else sts_u32(dlo_a + (uint32_t)(((warp * KS + ks) * 32 + lane) * 8 + 4 * h), pack_bf16(v0 - h0, v1 - h1));
             }
         }
     }
@@ -480,7 +494,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 }
                 {   // k-step ks into accumulator 0
                     uint32_t dl0, dl1;
-                    lds_u2(dlo_a + (uint32_t)(((warp * KS + ks) * 32 + lane) * 8), dl0, dl1);
+                    if constexpr (DL_REG) {
+                        dl0 = dlr[ks][0];
+                        dl1 = dlr[ks][1];
+                    } else {
+                        lds_u2(dlo_a + (uint32_t)(((warp * KS + ks) * 32 + lane) * 8), dl0, dl1);
+                    }
                     if (F32) {
                         uint32_t b0b, b0s, b1b, b1s;
                         tf32_split(p0, b0b, b0s);
@@ -496,7 +515,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 if (ks + 1 < KS) {   // k-step ks + 1 into accumulator 1
                     const int k1 = ks + 1 < KS ? ks + 1 : 0;   // in range for the unrolled copy
                     uint32_t dl0, dl1;
-                    lds_u2(dlo_a + (uint32_t)(((warp * KS + k1) * 32 + lane) * 8), dl0, dl1);
+                    if constexpr (DL_REG) {
+                        dl0 = dlr[k1][0];
+                        dl1 = dlr[k1][1];
+                    } else {
+                        lds_u2(dlo_a + (uint32_t)(((warp * KS + k1) * 32 + lane) * 8), dl0, dl1);
+                    }
                     if (F32) {
                         uint32_t b0b, b0s, b1b, b1s;
                         tf32_split(p2, b0b, b0s);
