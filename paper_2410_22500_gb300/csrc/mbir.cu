@@ -87,13 +87,10 @@ __global__ void __launch_bounds__(1024) mbir_update_kernel(const float *__restri
                                                            float *__restrict__ znext, ProjTables t,
                                                            const float *__restrict__ dA, const MbirChan *__restrict__ chp,
                                                            MbirPrior pr, float mom_a, int N, int Nc, int Nv, int Nr,
-                                                           int K, int Wl) {
-    const int CH = Wl / VW;
-    const int ipb = blockDim.x / CH;
-    const int pix = blockIdx.x * ipb + threadIdx.x / CH;
-    const int ch = threadIdx.x % CH;
-    if (threadIdx.x >= ipb * CH || pix >= N * N) return;
-    mbir_update_at<VW>(e, z, xprev, xnew, znext, t, dA, chp, pr, mom_a, N, Nc, Nv, Nr, K, Wl, pix, ch);
+                                                           int K, int Wl, int Wc) {
+    const GatherIdx gi = gather_idx<VW>(N * N, Wl, Wc);
+    if (!gi.ok) return;
+    mbir_update_at<VW>(e, z, xprev, xnew, znext, t, dA, chp, pr, mom_a, N, Nc, Nv, Nr, K, Wl, gi.item, gi.w0);
 }
 
 struct MbirWs {
@@ -137,10 +134,10 @@ static fhr_status check_mbir(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_par
 template <int VW>
 static fhr_status launch_update(fhr_ctx *ctx, const fhr_geom *g, const MbirWs &w, const float *z, const float *xp,
                                 float *xn, float *zn, const MbirPrior &pr, float a, int K, int Wl) {
-    const GatherShape s = gather_shape(Wl);
-    const unsigned blocks = (unsigned)cdiv((int64_t)g->N * g->N, s.ipb);
+    const GatherShape s = gather_shape(Wl, std::max((size_t)g->N * g->N, (size_t)g->Nv * g->Nc));
+    const unsigned blocks = s.blocks(g->N * g->N, Wl);
     FHR_TIMED(TM_MBIR_UPDATE, (mbir_update_kernel<VW><<<blocks, s.threads, 0, ctx->stream>>>(
-                                  w.e, z, xp, xn, zn, w.t, w.dA, w.chan, pr, a, g->N, g->Nc, g->Nv, g->Nr, K, Wl)));
+                                  w.e, z, xp, xn, zn, w.t, w.dA, w.chan, pr, a, g->N, g->Nc, g->Nv, g->Nr, K, Wl, s.wc)));
     return FHR_OK;
 }
 

@@ -53,17 +53,17 @@ __device__ __forceinline__ void mbir_update_at(const float *__restrict__ e, cons
                                                float *__restrict__ znext, const ProjTables &t,
                                                const float *__restrict__ dA, const MbirChan *__restrict__ chp,
                                                const MbirPrior &pr, float mom_a, int N, int Nc, int Nv, int Nr, int K,
-                                               int Wl, int pix, int ch) {
+                                               int Wl, int pix, int w0) {
     using VF = VecF<VW>;
-    const typename VF::T bp = backproject_at<VW, COH>(e, t, N, Nc, Nv, Wl, pix, ch);
+    const typename VF::T bp = backproject_at<VW, COH>(e, t, N, Nc, Nv, Wl, pix, w0);
     const int iy = pix / N, ix = pix % N;
-    const size_t base = (size_t)pix * Wl + ch * VW;
+    const size_t base = (size_t)pix * Wl + w0;
     const typename VF::T zc = ldv<VW, COH>(z + base);
     const float da = dA[pix];
     float g[VW], d[VW];
 #pragma unroll
     for (int q = 0; q < VW; ++q) {
-        const int j = (ch * VW + q) % K;
+        const int j = (w0 + q) % K;
         g[q] = -VF::get(bp, q) * chp->inv_sv2[j];
         d[q] = da * chp->inv_sv2[j];
     }
@@ -75,10 +75,10 @@ __device__ __forceinline__ void mbir_update_at(const float *__restrict__ e, cons
             const int yy = iy + dy8[n], xx = ix + dx8[n];
             if (yy < 0 || yy >= N || xx < 0 || xx >= N) continue;
             const float b = pr.beta * (n < 4 ? pr.b_edge : pr.b_diag);
-            const typename VF::T zn = ldv<VW, COH>(z + ((size_t)yy * N + xx) * Wl + ch * VW);
+            const typename VF::T zn = ldv<VW, COH>(z + ((size_t)yy * N + xx) * Wl + w0);
 #pragma unroll
             for (int q = 0; q < VW; ++q) {
-                const int j = (ch * VW + q) % K;
+                const int j = (w0 + q) % K;
                 const float dl = VF::get(zc, q) - VF::get(zn, q);
                 const float wt = qggmrf_infl(dl, chp->c0[j], chp->inv_tsx[j], pr.e, pr.c1);
                 g[q] = fmaf(b * dl, wt, g[q]);
@@ -88,7 +88,7 @@ __device__ __forceinline__ void mbir_update_at(const float *__restrict__ e, cons
         if (Nr > 1) {
 #pragma unroll
             for (int q = 0; q < VW; ++q) {
-                const int w = ch * VW + q;
+                const int w = w0 + q;
                 const int j = w % K, r = w / K;
                 const float b = pr.beta * pr.b_slice;
                 const float zq = VF::get(zc, q);

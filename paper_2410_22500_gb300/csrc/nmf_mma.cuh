@@ -9,18 +9,23 @@
 //   warps           phase 1 (tile t): partial r = D^T p for the 8 rows over
 //                   its bins with warp MMAs (D^T as the 16 x k operand: rows
 //                   0..7 its high, rows 8..15 its low part; P^T as the k x 8
-//                   operand), written to shared memory; phase 3 (tile t-1): Q += P^T w over its bins
-//                   (P^T as the 16 x k operand, w as the k x 8 operand), Q in
-//                   MMA accumulators for the whole launch;
+//                   operand), written to shared memory; phase 3 (tile
+//                   t - LAG): Q += P^T w over its bins (P^T as the 16 x k
+//                   operand, w as the k x 8 operand), Q in MMA accumulators
+//                   for the whole launch;
 //   2 update warps  (alternate tiles) sum the 13 partials of r, run the HALS
 //                   V half-step of the 8 pixels and write W; they stage w
 //                   for phase 3, where consumer warp 0 also adds w^T w to G_W
 //                   with two more MMAs.
+// The update warps and the producer sit on one SM sub-partition with a single
+// consumer warp (warps w and w + 4k share one), since the update is
+// latency-bound; with LAG = 2 its latency is off the per-tile critical path.
 //
 // Precision.  f32 P: TF32 products with the three-term split x = big + small
-// (big = x rounded to TF32, small = x - big) for P, D and w, dropping only
-// small*small, so products carry ~22 bits; bf16 P: P is exact in bf16, D and
-// w are split into bf16 hi + lo (~16 bits).  Accumulation is FP32 in both.
+// (big = x rounded or truncated to TF32, small = x - big) for P, D and w,
+// dropping only small*small (D's small part is kept to bf16, 2^-20 of D), so
+// products carry ~20 bits; bf16 P: P is exact in bf16, D and w are split into
+// bf16 hi + lo (~16 bits).  Accumulation is FP32 in both.
 #pragma once
 
 #include "nmf_pass.cuh"
@@ -39,7 +44,7 @@ __host__ __device__ inline int mma_nkw(int ldP) {
 }
 
 struct MmaSmem {
-    size_t tiles, wst, wb, red, dlo, gsm, invd, wsc, ssq, bars, total;
+    size_t tiles, wst, wb, red, gsm, invd, wsc, ssq, bars, total;
     uint32_t rs;   // bytes per staged pixel row
 };
 
@@ -59,8 +64,6 @@ __host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stage
     L.wst = take((size_t)stages * kMmaRows * kMaxK * sizeof(float), 128);   // W rows of each staged tile
     L.wb = take((size_t)nb * 2 * 8 * kMmaWbStride, 128);     // [buffer][big|small or hi|lo][s][48 B]
     L.red = take((size_t)nb * 16 * 64 * sizeof(float), 16);   // [buffer][warp, padded to 16][row][s]
-    // f32: low parts of the D^T fragments, [warp][k-step][lane] x {a0, a2} (bf16 keeps them in registers)
-    L.dlo = take(esize == 4 ? (size_t)kMmaCW * (mma_nkw(ldP) / 8) * 32 * 8 : 0, 16);
     L.gsm = take((size_t)kMaxK * kMaxK * sizeof(float), 16);
     L.invd = take((size_t)kMaxK * sizeof(float), 16);
     L.wsc = take((size_t)kMaxK * sizeof(float), 16);
@@ -200,7 +203,6 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     const uint32_t tiles_a = sb + (uint32_t)Lyt.tiles;
     const uint32_t wb_a = sb + (uint32_t)Lyt.wb;
     const uint32_t red_a = sb + (uint32_t)Lyt.red;
-    const uint32_t dlo_a = sb + (uint32_t)Lyt.dlo;
     const float *wst = reinterpret_cast<const float *>(smem + Lyt.wst);
     const bool reads_w = a.mode == PASS_HALS || a.mode == PASS_GIVEN_W;
     float *gsm = reinterpret_cast<float *>(smem + Lyt.gsm);
@@ -428,9 +430,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     // D^T fragments, the 16 x k operand of phase 1: rows 0..7 the high parts
     // (registers), rows 8..15 the low parts (shared memory), [k-step][a0/a1, a2/a3]
     uint32_t da[KS][2];   // f32: big; bf16: hi
-    // bf16 keeps the low parts in registers too (fewer registers per bin than f32)
-    constexpr bool DL_REG = !F32;
-    uint32_t dlr[DL_REG ? KS : 1][2];
+    // low parts in registers: bf16 as they are; f32 (TF32 remainders, below 2^-11 of
+    // the value) rounded to bf16 and packed two to a register
+    uint32_t dlr[KS][F32 ? 1 : 2];
 #pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
 #pragma unroll
@@ -440,8 +442,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 const float v = (g < K && k < a.Nk) ? (float)(a.D64[(size_t)k * K + g] * a.st->invn[g]) : 0.f;
                 const uint32_t big = tf32_big(v);
                 da[ks][h] = big;
-                sts_u32(dlo_a + (uint32_t)(((warp * KS + ks) * 32 + lane) * 8 + 4 * h),
-                        __float_as_uint(v - __uint_as_float(big)));
+                const uint32_t sb16 = (uint32_t)bf16_bits(v - __uint_as_float(big));
+                dlr[ks][0] = h ? (dlr[ks][0] | (sb16 << 16)) : sb16;
             } else {
                 const int k = c0 + ks * 16 + 2 * tig + 8 * h;
                 float v0 = 0.f, v1 = 0.f;
@@ -450,8 +452,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 const float h0 = __bfloat162float(__float2bfloat16_rn(v0));
                 const float h1 = __bfloat162float(__float2bfloat16_rn(v1));
                 da[ks][h] = pack_bf16(v0, v1);
-                if constexpr (DL_REG) dlr[ks][h] = pack_bf16(v0 - h0, v1 - h1);
-                else sts_u32(dlo_a + (uint32_t)(((warp * KS + ks) * 32 + lane) * 8 + 4 * h), pack_bf16(v0 - h0, v1 - h1));
+                dlr[ks][h] = pack_bf16(v0 - h0, v1 - h1);
             }
         }
     }
@@ -494,11 +495,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 }
                 {   // k-step ks into accumulator 0
                     uint32_t dl0, dl1;
-                    if constexpr (DL_REG) {
-                        dl0 = dlr[ks][0];
-                        dl1 = dlr[ks][1];
+                    if constexpr (F32) {   // TF32 patterns of the bf16-rounded remainders
+                        dl0 = dlr[ks][0] << 16;
+                        dl1 = dlr[ks][0] & 0xffff0000u;
                     } else {
-                        lds_u2(dlo_a + (uint32_t)(((warp * KS + ks) * 32 + lane) * 8), dl0, dl1);
+                        dl0 = dlr[ks][0];
+                        dl1 = dlr[ks][F32 ? 0 : 1];
                     }
                     if (F32) {
                         uint32_t b0b, b0s, b1b, b1s;
@@ -515,11 +517,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 if (ks + 1 < KS) {   // k-step ks + 1 into accumulator 1
                     const int k1 = ks + 1 < KS ? ks + 1 : 0;   // in range for the unrolled copy
                     uint32_t dl0, dl1;
-                    if constexpr (DL_REG) {
-                        dl0 = dlr[k1][0];
-                        dl1 = dlr[k1][1];
+                    if constexpr (F32) {
+                        dl0 = dlr[k1][0] << 16;
+                        dl1 = dlr[k1][0] & 0xffff0000u;
                     } else {
-                        lds_u2(dlo_a + (uint32_t)(((warp * KS + k1) * 32 + lane) * 8), dl0, dl1);
+                        dl0 = dlr[k1][0];
+                        dl1 = dlr[k1][F32 ? 0 : 1];
                     }
                     if (F32) {
                         uint32_t b0b, b0s, b1b, b1s;

@@ -35,11 +35,11 @@ PassFn<__nv_bfloat16> pick<__nv_bfloat16>(int K, int cpt) {
 }
 #undef CASE
 
-// pipeline lag of the tensor-core pass per element type (bf16 tiles are half
-// the size, so the ring has room for the deeper hand-off)
+// pipeline lag of the tensor-core pass: phase 3 two tiles behind phase 1 (the
+// ring still holds two tiles in flight for rows up to ~1300 f32 bins)
 template <typename TP>
 struct MmaLag {
-    static constexpr int V = sizeof(TP) == 2 ? 2 : 1;
+    static constexpr int V = 2;
 };
 
 template <typename TP>

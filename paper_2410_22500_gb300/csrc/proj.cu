@@ -123,30 +123,33 @@ fhr_status proj_build_tables(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &
     return FHR_OK;
 }
 
+// values per channel of the larger of the image and the sinogram
+static size_t slab_values(const fhr_geom *g) {
+    return std::max((size_t)g->N * g->N, (size_t)g->Nv * g->Nc);
+}
+
 fhr_status proj_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *x, float *y,
                         const float *V) {
-    const GatherShape s = gather_shape(Wl);
-    const int items = g->Nv * g->Nc;
-    const unsigned blocks = (unsigned)cdiv(items, s.ipb);
+    const GatherShape s = gather_shape(Wl, slab_values(g));
+    const unsigned blocks = s.blocks(g->Nv * g->Nc, Wl);
     if (s.vw == 4)
         FHR_TIMED(TM_PROJ_FWD, (proj_fwd_kernel<4><<<blocks, s.threads, 0, ctx->stream>>>(x, y, V, t, g->N, g->Nc,
-                                                                                          g->Nv, Wl)));
+                                                                                          g->Nv, Wl, s.wc)));
     else
         FHR_TIMED(TM_PROJ_FWD, (proj_fwd_kernel<1><<<blocks, s.threads, 0, ctx->stream>>>(x, y, V, t, g->N, g->Nc,
-                                                                                          g->Nv, Wl)));
+                                                                                          g->Nv, Wl, s.wc)));
     return FHR_OK;
 }
 
 fhr_status proj_backward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *y, float *x) {
-    const GatherShape s = gather_shape(Wl);
-    const int items = g->N * g->N;
-    const unsigned blocks = (unsigned)cdiv(items, s.ipb);
+    const GatherShape s = gather_shape(Wl, slab_values(g));
+    const unsigned blocks = s.blocks(g->N * g->N, Wl);
     if (s.vw == 4)
         FHR_TIMED(TM_PROJ_BWD, (proj_bwd_kernel<4><<<blocks, s.threads, 0, ctx->stream>>>(y, x, t, g->N, g->Nc,
-                                                                                          g->Nv, Wl)));
+                                                                                          g->Nv, Wl, s.wc)));
     else
         FHR_TIMED(TM_PROJ_BWD, (proj_bwd_kernel<1><<<blocks, s.threads, 0, ctx->stream>>>(y, x, t, g->N, g->Nc,
-                                                                                          g->Nv, Wl)));
+                                                                                          g->Nv, Wl, s.wc)));
     return FHR_OK;
 }
 

@@ -80,10 +80,10 @@ __device__ __forceinline__ typename VecF<VW>::T ldv(const float *p) {
 }
 
 // sum over lines and candidates of A * x[pixel][w] for one ray (item = (v, c)),
-// chunk ch of VW values.
+// the VW values w0 .. w0 + VW - 1.
 template <int VW, bool COH = false>
 __device__ __forceinline__ typename VecF<VW>::T forward_at(const float *__restrict__ x, const ProjTables &t, int N,
-                                                           int Nc, int Wl, int item, int ch) {
+                                                           int Nc, int Wl, int item, int w0) {
     using VF = VecF<VW>;
     const int v = item / Nc, c = item - v * Nc;
     const bool rows = t.rowmaj[v] != 0;
@@ -92,7 +92,7 @@ __device__ __forceinline__ typename VecF<VW>::T forward_at(const float *__restri
     const int lstride = rows ? N : 1;     // pixel index = l * lstride + q * qstride
     const int qstride = rows ? 1 : N;
     typename VF::T acc = VF::zero();
-    const float *xc = x + ch * VW;
+    const float *xc = x + w0;
     for (int l = 0; l < N; ++l) {
         const float4 w = __ldg(fw + (size_t)l * Nc);
         const int s0 = __ldg(fs + (size_t)l * Nc);
@@ -105,23 +105,42 @@ __device__ __forceinline__ typename VecF<VW>::T forward_at(const float *__restri
     return acc;
 }
 
+// Gathers over a vector of Wl values per pixel / ray run in channel chunks of
+// Wc values (Wc | Wl, VW | Wc), chunk-major over the grid: the blocks resident
+// at one time touch one chunk of the image / sinogram, which stays in L2 when
+// the whole does not.  Thread = (item, VW values of the chunk).
+struct GatherIdx {
+    int item, w0;
+    bool ok;
+};
+
+template <int VW>
+__device__ __forceinline__ GatherIdx gather_idx(int items, int Wl, int Wc) {
+    const int CH = Wc / VW;
+    const int ipb = blockDim.x / CH;
+    const int bpc = (items + ipb - 1) / ipb;   // blocks per chunk
+    const int chunk = blockIdx.x / bpc;
+    GatherIdx r;
+    r.item = (blockIdx.x - chunk * bpc) * ipb + threadIdx.x / CH;
+    r.w0 = chunk * Wc + (threadIdx.x % CH) * VW;
+    r.ok = threadIdx.x < ipb * CH && r.item < items && r.w0 < Wl;
+    return r;
+}
+
 // y[v][c][w] = sum over lines and candidates of A * x[pixel][w].
-// Thread = (item (v, c), chunk of VW values).  With V non-null the output is
-// the residual V - A x.
+// With V non-null the output is the residual V - A x.
 template <int VW>
 __global__ void __launch_bounds__(1024) proj_fwd_kernel(const float *__restrict__ x, float *__restrict__ y,
                                                         const float *__restrict__ V, ProjTables t, int N, int Nc,
-                                                        int Nv, int Wl) {
+                                                        int Nv, int Wl, int Wc) {
     using VF = VecF<VW>;
-    const int CH = Wl / VW;
-    const int ipb = blockDim.x / CH;
-    const int item = blockIdx.x * ipb + threadIdx.x / CH;
-    const int ch = threadIdx.x % CH;
-    if (threadIdx.x >= ipb * CH || item >= Nv * Nc) return;
-    typename VF::T acc = forward_at<VW>(x, t, N, Nc, Wl, item, ch);
-    float *yo = y + (size_t)item * Wl + ch * VW;
+    const GatherIdx gi = gather_idx<VW>(Nv * Nc, Wl, Wc);
+    if (!gi.ok) return;
+    const int item = gi.item;
+    typename VF::T acc = forward_at<VW>(x, t, N, Nc, Wl, item, gi.w0);
+    float *yo = y + (size_t)item * Wl + gi.w0;
     if (V) {
-        typename VF::T vv = VF::ld(V + (size_t)item * Wl + ch * VW);
+        typename VF::T vv = VF::ld(V + (size_t)item * Wl + gi.w0);
 #pragma unroll
         for (int e = 0; e < VW; ++e) VF::set(acc, e, VF::get(vv, e) - VF::get(acc, e));
     }
@@ -131,10 +150,10 @@ __global__ void __launch_bounds__(1024) proj_fwd_kernel(const float *__restrict_
 // x[pixel][w] = sum over views and candidate bins of A * y[v][c][w].
 template <int VW, bool COH = false>
 __device__ __forceinline__ typename VecF<VW>::T backproject_at(const float *__restrict__ y, const ProjTables &t, int N,
-                                                               int Nc, int Nv, int Wl, int pix, int ch) {
+                                                               int Nc, int Nv, int Wl, int pix, int w0) {
     using VF = VecF<VW>;
     typename VF::T acc = VF::zero();
-    const float *yc = y + ch * VW;
+    const float *yc = y + w0;
     const size_t NN = (size_t)N * N;
     for (int v = 0; v < Nv; ++v) {
         const float4 w = __ldg(t.bk + v * NN + pix);
@@ -148,26 +167,35 @@ __device__ __forceinline__ typename VecF<VW>::T backproject_at(const float *__re
 
 template <int VW>
 __global__ void __launch_bounds__(1024) proj_bwd_kernel(const float *__restrict__ y, float *__restrict__ x,
-                                                        ProjTables t, int N, int Nc, int Nv, int Wl) {
+                                                        ProjTables t, int N, int Nc, int Nv, int Wl, int Wc) {
     using VF = VecF<VW>;
-    const int CH = Wl / VW;
-    const int ipb = blockDim.x / CH;
-    const int pix = blockIdx.x * ipb + threadIdx.x / CH;
-    const int ch = threadIdx.x % CH;
-    if (threadIdx.x >= ipb * CH || pix >= N * N) return;
-    VF::st(x + (size_t)pix * Wl + ch * VW, backproject_at<VW>(y, t, N, Nc, Nv, Wl, pix, ch));
+    const GatherIdx gi = gather_idx<VW>(N * N, Wl, Wc);
+    if (!gi.ok) return;
+    VF::st(x + (size_t)gi.item * Wl + gi.w0, backproject_at<VW>(y, t, N, Nc, Nv, Wl, gi.item, gi.w0));
 }
 
-// Launch shape for the gathers: CH = Wl / VW threads per item, items per block
-// so that a block holds about `target` threads.
+// Launch shape for the gathers: chunks of Wc values (the whole vector unless
+// the larger of the image / sinogram slabs exceeds kGatherSlab bytes), CH =
+// Wc / VW threads per item, items per block so that a block holds about
+// `target` threads, and the grid = chunks x blocks per chunk.
+constexpr size_t kGatherSlab = (size_t)32 << 20;
+
 struct GatherShape {
-    int vw, ch, ipb, threads;
+    int vw, wc, ch, ipb, threads;
+    unsigned blocks(int items, int Wl) const {
+        const int bpc = (items + ipb - 1) / ipb;
+        return (unsigned)(bpc * (Wl / wc));
+    }
 };
 
-static inline GatherShape gather_shape(int Wl, int target = 256) {
+static inline GatherShape gather_shape(int Wl, size_t slab_values = 0, int target = 256) {
     GatherShape g;
     g.vw = (Wl % 4 == 0) ? 4 : 1;
-    g.ch = Wl / g.vw;
+    g.wc = Wl;
+    // halve the chunk while the slab of one chunk exceeds the L2 budget (keeping VW | Wc | Wl)
+    while (slab_values * (size_t)g.wc * sizeof(float) > kGatherSlab && g.wc % (2 * g.vw) == 0 && g.wc / 2 >= 32)
+        g.wc /= 2;
+    g.ch = g.wc / g.vw;
     g.ipb = std::max(1, target / g.ch);
     g.threads = g.ipb * g.ch;
     return g;
