@@ -368,6 +368,13 @@ typedef struct {
     int recon;   /* FHR_RECON_MBIR (Eq. recon, default) or FHR_RECON_FBP (fhr_fbp) */
 } fhr_pipeline_params;
 
+/* With host_io, y and y0 are pinned host buffers copied in on a copy stream
+ * and xh a pinned host buffer copied out on another: the call returns with the
+ * output copy pending, and consecutive calls overlap their copies with each
+ * other's compute.  The host buffers must stay untouched until the copies
+ * are done: fhr_io_join orders the context stream after the last output copy,
+ * and fhr_workspace_status waits for it (as does a device synchronisation). */
+fhr_status fhr_io_join(fhr_ctx *ctx);
 fhr_status fhr_pipeline_workspace_size(fhr_ctx *ctx, const fhr_pipeline_params *prm, size_t *bytes);
 fhr_status fhr_pipeline(fhr_ctx *ctx, const fhr_pipeline_params *prm,
                         const uint16_t *y, const uint16_t *y0,

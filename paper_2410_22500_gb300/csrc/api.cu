@@ -102,6 +102,16 @@ extern "C" fhr_status fhr_create(fhr_ctx **out, int device, void *stream) {
 
 extern "C" void fhr_destroy(fhr_ctx *ctx) {
     if (!ctx) return;
+    if (ctx->io_ready) {
+        cudaStreamSynchronize(ctx->io_h2d);
+        cudaStreamSynchronize(ctx->io_d2h);
+        cudaEventDestroy(ctx->ev_in_ready);
+        cudaEventDestroy(ctx->ev_in_free);
+        cudaEventDestroy(ctx->ev_out_ready);
+        cudaEventDestroy(ctx->ev_out_free);
+        cudaStreamDestroy(ctx->io_h2d);
+        cudaStreamDestroy(ctx->io_d2h);
+    }
     for (int i = 0; i < TM_COUNT; ++i) {
         for (int j = 0; j < 2 * ctx->tm[i].cap; ++j) cudaEventDestroy(ctx->tm[i].ev[j]);
         free(ctx->tm[i].ev);
@@ -119,10 +129,19 @@ extern "C" const char *fhr_last_error(const fhr_ctx *ctx) { return ctx ? ctx->er
 
 extern "C" const char *fhr_version(void) { return "libfhr 0.1 (sm_103a)"; }
 
+extern "C" fhr_status fhr_io_join(fhr_ctx *ctx) {
+    if (!ctx) return FHR_ERR_ARG;
+    if (!ctx->io_ready) return FHR_OK;
+    FHR_CUDA(cudaSetDevice(ctx->device));
+    FHR_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_out_free, 0));
+    return FHR_OK;
+}
+
 extern "C" fhr_status fhr_workspace_status(fhr_ctx *ctx, void *ws) {
     if (!ctx) return FHR_ERR_ARG;
     FHR_ARG(ws, "workspace is null");
     FHR_CUDA(cudaSetDevice(ctx->device));
+    if (ctx->io_ready) FHR_CUDA(cudaStreamSynchronize(ctx->io_d2h));
     int st = 0;
     FHR_CUDA(cudaMemcpyAsync(&st, ws, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     FHR_CUDA(cudaStreamSynchronize(ctx->stream));

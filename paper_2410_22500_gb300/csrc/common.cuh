@@ -28,6 +28,10 @@ struct fhr_ctx {
         cudaEvent_t *ev;       // pairs (start, stop)
         int used, cap;
     } tm[TM_COUNT];
+    // host I/O of the pipeline: copy streams and the events that order them
+    int io_ready;
+    cudaStream_t io_h2d, io_d2h;
+    cudaEvent_t ev_in_ready, ev_in_free, ev_out_ready, ev_out_free;
 };
 
 namespace fhr {

@@ -12,6 +12,17 @@ size_t fbp_ws_bytes(const fhr_geom *g, int Wl);
 fhr_status expand_impl(fhr_ctx *ctx, int N, int Nr, int K, int Nk, int k0, int k1, const float *xs, const float *D,
                        int dt, void *xh);
 
+// Copy streams of the host-I/O form, created on first use.
+static fhr_status io_init(fhr_ctx *ctx) {
+    if (ctx->io_ready) return FHR_OK;
+    FHR_CUDA(cudaStreamCreateWithFlags(&ctx->io_h2d, cudaStreamNonBlocking));
+    FHR_CUDA(cudaStreamCreateWithFlags(&ctx->io_d2h, cudaStreamNonBlocking));
+    cudaEvent_t *evs[4] = {&ctx->ev_in_ready, &ctx->ev_in_free, &ctx->ev_out_ready, &ctx->ev_out_free};
+    for (cudaEvent_t *e : evs) FHR_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    ctx->io_ready = 1;
+    return FHR_OK;
+}
+
 struct PipeWs {
     int *status;
     uint16_t *y, *y0;
@@ -100,12 +111,20 @@ extern "C" fhr_status fhr_pipeline(fhr_ctx *ctx, const fhr_pipeline_params *p, c
     const uint16_t *yd = y, *y0d = y0;
     const size_t ny = (size_t)n.Nv * n.Nr * n.Nc * n.Nk, ny0 = (size_t)n.Nr * n.Nc * n.Nk;
     if (p->host_io) {
-        FHR_CUDA(cudaMemcpyAsync(w.y, y, ny * 2, cudaMemcpyHostToDevice, st));
-        FHR_CUDA(cudaMemcpyAsync(w.y0, y0, ny0 * 2, cudaMemcpyHostToDevice, st));
+        // Host I/O runs on two copy streams, so consecutive calls overlap: this
+        // call's input copy waits only until the previous call has normalised its
+        // staged counts, and its output copy runs behind the next call's compute.
+        FHR_TRY(io_init(ctx));
+        FHR_CUDA(cudaStreamWaitEvent(ctx->io_h2d, ctx->ev_in_free, 0));
+        FHR_CUDA(cudaMemcpyAsync(w.y, y, ny * 2, cudaMemcpyHostToDevice, ctx->io_h2d));
+        FHR_CUDA(cudaMemcpyAsync(w.y0, y0, ny0 * 2, cudaMemcpyHostToDevice, ctx->io_h2d));
+        FHR_CUDA(cudaEventRecord(ctx->ev_in_ready, ctx->io_h2d));
+        FHR_CUDA(cudaStreamWaitEvent(st, ctx->ev_in_ready, 0));
         yd = w.y;
         y0d = w.y0;
     }
     FHR_TRY(fhr_normalise(ctx, &n, yd, y0d, bg, dead, bg ? w.b : nullptr, w.P));
+    if (p->host_io) FHR_CUDA(cudaEventRecord(ctx->ev_in_free, st));
     FHR_TRY(fhr_decompose(ctx, &p->nmf, w.P, D_out, w.W, obj, w.nmf_ws, w.nmf_bytes));
     const size_t nxs = (size_t)p->geom.N * p->geom.N * n.Nr * K;
     FHR_CUDA(cudaMemsetAsync(w.xs, 0, nxs * sizeof(float), st));
@@ -114,12 +133,17 @@ extern "C" fhr_status fhr_pipeline(fhr_ctx *ctx, const fhr_pipeline_params *p, c
     else
         FHR_TRY(reconstruct_impl(ctx, &p->geom, &p->mbir, w.W, w.xs, w.mbir_ws, w.mbir_bytes));
     void *xo = p->host_io ? w.xh : xh;
+    // the staged output is reused once the previous call's output copy is done
+    if (p->host_io) FHR_CUDA(cudaStreamWaitEvent(st, ctx->ev_out_free, 0));
     FHR_TRY(expand_impl(ctx, p->geom.N, n.Nr, K, n.Nk, 0, 0, w.xs, D_out, p->xh_dtype, xo));
     gather_status<<<1, 32, 0, st>>>(w.status, (const int *)w.nmf_ws, (const int *)w.mbir_ws);
     FHR_LAUNCHED();
     if (p->host_io) {
         const size_t nxh = (size_t)n.Nr * p->geom.N * p->geom.N * n.Nk * (p->xh_dtype == FHR_BF16 ? 2 : 4);
-        FHR_CUDA(cudaMemcpyAsync(xh, w.xh, nxh, cudaMemcpyDeviceToHost, st));
+        FHR_CUDA(cudaEventRecord(ctx->ev_out_ready, st));
+        FHR_CUDA(cudaStreamWaitEvent(ctx->io_d2h, ctx->ev_out_ready, 0));
+        FHR_CUDA(cudaMemcpyAsync(xh, w.xh, nxh, cudaMemcpyDeviceToHost, ctx->io_d2h));
+        FHR_CUDA(cudaEventRecord(ctx->ev_out_free, ctx->io_d2h));
     }
     return FHR_OK;
 }

@@ -130,7 +130,7 @@ __device__ __forceinline__ GatherIdx gather_idx(int items, int Wl, int Wc) {
 // y[v][c][w] = sum over lines and candidates of A * x[pixel][w].
 // With V non-null the output is the residual V - A x.
 template <int VW>
-__global__ void __launch_bounds__(1024) proj_fwd_kernel(const float *__restrict__ x, float *__restrict__ y,
+__global__ void __launch_bounds__(1024, 2) proj_fwd_kernel(const float *__restrict__ x, float *__restrict__ y,
                                                         const float *__restrict__ V, ProjTables t, int N, int Nc,
                                                         int Nv, int Wl, int Wc) {
     using VF = VecF<VW>;

@@ -26,7 +26,7 @@ ENTRY_POINTS = (
     "fhr_pipeline_workspace_size", "fhr_pipeline", "fhr_profile_enable", "fhr_profile_read",
     "fhr_decompose_static", "fhr_mlp_workspace_size", "fhr_mlp_forward", "fhr_mlp_grad", "fhr_mlp_adamw",
     "fhr_reconstruct_batch_workspace_size", "fhr_reconstruct_batch", "fhr_reconstruct_batch_autotune",
-    "fhr_fbp_workspace_size", "fhr_fbp",
+    "fhr_fbp_workspace_size", "fhr_fbp", "fhr_io_join",
 )
 
 
@@ -125,6 +125,7 @@ def load():
         L.fhr_reconstruct_batch_workspace_size.argtypes = [vp, ctypes.c_int, PP, BP, szp]
         L.fhr_reconstruct_batch.argtypes = [vp, ctypes.c_int, PP, BP, vp, sz]
         L.fhr_reconstruct_batch_autotune.argtypes = [vp, ctypes.c_int, PP, BP, vp, sz, ctypes.POINTER(ctypes.c_int)]
+        L.fhr_io_join.argtypes = [vp]
         L.fhr_fbp_workspace_size.argtypes = [vp, ctypes.POINTER(Geom), ctypes.c_int, szp]
         L.fhr_fbp.argtypes = [vp, ctypes.POINTER(Geom), ctypes.c_int, vp, vp, vp, sz]
         L.fhr_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -458,6 +459,10 @@ class Context:
         prm.host_io = int(host_io)
         prm.recon = recon
         return prm
+
+    def io_join(self):
+        """Order the context stream after the last host-I/O output copy."""
+        self.check(self.L.fhr_io_join(self._h))
 
     def pipeline_workspace(self, prm):
         n = ctypes.c_size_t()

@@ -76,3 +76,33 @@ def test_small_3d_end_to_end(fx, orc):
     ref = orc.fhr_pipeline(y, y0, 3, g.N, g.angles(), nmf_iters=100, mbir_iters=20, dead=pb.dead_bins)
     assert _rel(xh.cpu().numpy(), ref["xh"]) <= 1e-3
     assert np.all(D.cpu().numpy()[pb.dead_bins.astype(bool)] == 0)
+
+
+def test_host_io_back_to_back_calls(fx):
+    # consecutive host-I/O calls on one workspace overlap their copies with each
+    # other's compute; each output must still be its own input's result
+    import torch
+
+    from paper_2410_22500_gb300 import synth
+
+    pa = synth.scaled(synth.tiny_2d, Nk=64, Nv=30)
+    pb = synth.scaled(synth.tiny_2d, Nk=64, Nv=30, seed=1234)
+    g = pa.geom
+    K = 3
+    prm = fx.pipeline_params(Nv=g.Nv, Nr=g.Nr, Nc=g.Nc, Nk=pa.Nk, N=g.N, K=K, nmf_iters=20, mbir_iters=5,
+                             host_io=True, seed=3)
+    ws, wsb = fx.pipeline_workspace(prm)
+    outs, refs = [], []
+    D = torch.empty((pa.Nk, K), dtype=torch.float32, device="cuda")
+    for pb_ in (pa, pb, pa):
+        y, y0 = synth.counts_numpy(pb_)
+        yt = torch.from_numpy(y.view(np.int16)).pin_memory()
+        y0t = torch.from_numpy(y0.view(np.int16)).pin_memory()
+        xh = torch.empty((g.Nr, g.N, g.N, pa.Nk), dtype=torch.float32).pin_memory()
+        fx.pipeline(prm, yt, y0t, D, xh, ws=ws, ws_bytes=wsb)
+        outs.append((xh, yt, y0t))
+    assert fx.status(ws) == 0
+    for pb_, (xh, _, _) in zip((pa, pb, pa), outs):
+        refs.append(_run_gpu(fx, pb_, K, 20, 5)[3])
+        np.testing.assert_array_equal(xh.numpy(), refs[-1])
+    assert not np.array_equal(refs[0], refs[1])
