@@ -15,6 +15,9 @@ Every function cites the passage of the paper it follows.  Parity status:
   expansion        pinned (identity dictionary, commutes with the projector)
   MLP warm start   pinned (closed-form activations, layer-wise numpy, central
                    differences of the loss, AdamW closed form)
+  FMD (semi-sup.)  pinned (hand-computed region means, exact recovery of a
+                   nonnegative material mix, KKT on noisy data, App. B
+                   identity D^m = D^s T^T recovering the material spectra)
   FBP variant      pinned (textbook ramp samples, filter = direct convolution
                    with the kernel, disk reconstruction from analytic chords)
   clustering start pinned (published splitmix64 outputs, separated clusters
@@ -393,6 +396,46 @@ def fhr_pipeline(y, y0, K, N, theta, *, nmf_iters=200, mbir_iters=20, dead=None,
         xs = mbir(V, N, Nr, K, theta, sv, sx, p=p, T=T, iters=mbir_iters, momentum=momentum)
     xh = expand(xs, D, N, Nr)
     return dict(P=P, D0=D0, W0=W0, D=D, W=W, obj=obj, sv=sv, sx=sx, xs=xs, xh=xh)
+
+
+# ---------------------------------------------------------------- FMD, semi-supervised (Algorithm 2)
+def fmd_transform(xs, labels, Nm):
+    """Eq. trans_mat: T[i][j] = mean of x^s_{n,j} over the voxels n of region i
+    (labels[n] = i + 1; 0 = in no region).  xs [Nx][Ns] -> T [Nm][Ns]."""
+    xs = _f64(xs)
+    labels = np.asarray(labels).reshape(-1)
+    T = np.zeros((Nm, xs.shape[1]))
+    for i in range(Nm):
+        sel = xs[labels == i + 1]
+        if len(sel):
+            T[i] = sel.mean(axis=0)
+    return T
+
+
+def fmd_materials(xs, T):
+    """Eq. mat_recon_nmf: x^m = argmin_{x >= 0} ||x^s - x T||_F^2, one nonnegative
+    least-squares problem per voxel (scipy's Lawson-Hanson NNLS as the solver)."""
+    from scipy.optimize import nnls
+
+    xs = _f64(xs)
+    T = _f64(T)
+    xm = np.zeros((xs.shape[0], T.shape[0]))
+    A = T.T.copy()
+    for n in range(xs.shape[0]):
+        xm[n], _ = nnls(A, xs[n])
+    return xm
+
+
+def fmd_spectra(D, T):
+    """Eq. sub_mat_rel_basis: D^m = D^s T^T."""
+    return _f64(D) @ _f64(T).T
+
+
+def fmd(xs, D, labels, Nm):
+    """Algorithm 2 after the reconstruction, semi-supervised (user regions):
+    returns (T, x^m, D^m)."""
+    T = fmd_transform(xs, labels, Nm)
+    return T, fmd_materials(xs, T), fmd_spectra(D, T)
 
 
 # ---------------------------------------------------------------- learned warm start (MLP)
