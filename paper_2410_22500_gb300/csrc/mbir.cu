@@ -81,16 +81,16 @@ __global__ void fill_kernel(float *x, int64_t n, float v) {
         x[i] = v;
 }
 
-template <int VW>
+template <int VW, int G>
 __global__ void __launch_bounds__(1024) mbir_update_kernel(const float *__restrict__ e, const float *__restrict__ z,
                                                            const float *__restrict__ xprev, float *__restrict__ xnew,
                                                            float *__restrict__ znext, ProjTables t,
                                                            const float *__restrict__ dA, const MbirChan *__restrict__ chp,
                                                            MbirPrior pr, float mom_a, int N, int Nc, int Nv, int Nr,
                                                            int K, int Wl, int Wc) {
-    const GatherIdx gi = gather_idx<VW>(N * N, Wl, Wc);
+    const GatherIdx gi = gather_idx<VW * G>(N * N, Wl, Wc);
     if (!gi.ok) return;
-    mbir_update_at<VW>(e, z, xprev, xnew, znext, t, dA, chp, pr, mom_a, N, Nc, Nv, Nr, K, Wl, gi.item, gi.w0);
+    mbir_update_at<VW, G>(e, z, xprev, xnew, znext, t, dA, chp, pr, mom_a, N, Nc, Nv, Nr, K, Wl, gi.item, gi.w0);
 }
 
 struct MbirWs {
@@ -131,14 +131,22 @@ static fhr_status check_mbir(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_par
     return FHR_OK;
 }
 
-template <int VW>
+template <int VW, int G>
+static fhr_status launch_update_g(fhr_ctx *ctx, const fhr_geom *g, const GatherShape &s, const MbirWs &w,
+                                  const float *z, const float *xp, float *xn, float *zn, const MbirPrior &pr, float a,
+                                  int K, int Wl) {
+    FHR_TIMED(TM_MBIR_UPDATE, (mbir_update_kernel<VW, G><<<s.blocks(g->N * g->N, Wl), s.threads, 0, ctx->stream>>>(
+                                  w.e, z, xp, xn, zn, w.t, w.dA, w.chan, pr, a, g->N, g->Nc, g->Nv, g->Nr, K, Wl,
+                                  s.wc)));
+    return FHR_OK;
+}
+
 static fhr_status launch_update(fhr_ctx *ctx, const fhr_geom *g, const MbirWs &w, const float *z, const float *xp,
                                 float *xn, float *zn, const MbirPrior &pr, float a, int K, int Wl) {
-    const GatherShape s = gather_shape(Wl, std::max((size_t)g->N * g->N, (size_t)g->Nv * g->Nc));
-    const unsigned blocks = s.blocks(g->N * g->N, Wl);
-    FHR_TIMED(TM_MBIR_UPDATE, (mbir_update_kernel<VW><<<blocks, s.threads, 0, ctx->stream>>>(
-                                  w.e, z, xp, xn, zn, w.t, w.dA, w.chan, pr, a, g->N, g->Nc, g->Nv, g->Nr, K, Wl, s.wc)));
-    return FHR_OK;
+    const GatherShape s = gather_shape(Wl, gather_slab_values(g));
+    if (s.vw == 4 && s.g == 2) return launch_update_g<4, 2>(ctx, g, s, w, z, xp, xn, zn, pr, a, K, Wl);
+    if (s.vw == 4) return launch_update_g<4, 1>(ctx, g, s, w, z, xp, xn, zn, pr, a, K, Wl);
+    return launch_update_g<1, 1>(ctx, g, s, w, z, xp, xn, zn, pr, a, K, Wl);
 }
 
 fhr_status reconstruct_impl(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_params *p, const float *sino, float *xs,
@@ -199,7 +207,6 @@ fhr_status reconstruct_impl(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_para
     if (p->momentum) FHR_CUDA(cudaMemcpyAsync(Z0, xs, xbytes, cudaMemcpyDeviceToDevice, st));
     else Z0 = X0;
     double tk = 1.0;
-    const bool v4 = Wl % 4 == 0;
     for (int it = 0; it < p->iters; ++it) {
         FHR_TRY(proj_forward(ctx, g, w.t, Wl, Z0, w.e, sino));
         float a = 0.f;
@@ -207,13 +214,11 @@ fhr_status reconstruct_impl(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_para
             const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
             a = (float)((tk - 1.0) / tn);
             tk = tn;
-            if (v4) FHR_TRY(launch_update<4>(ctx, g, w, Z0, X0, X1, Z1, pr, a, K, Wl));
-            else FHR_TRY(launch_update<1>(ctx, g, w, Z0, X0, X1, Z1, pr, a, K, Wl));
+            FHR_TRY(launch_update(ctx, g, w, Z0, X0, X1, Z1, pr, a, K, Wl));
             std::swap(X0, X1);
             std::swap(Z0, Z1);
         } else {
-            if (v4) FHR_TRY(launch_update<4>(ctx, g, w, Z0, nullptr, X1, nullptr, pr, 0.f, K, Wl));
-            else FHR_TRY(launch_update<1>(ctx, g, w, Z0, nullptr, X1, nullptr, pr, 0.f, K, Wl));
+            FHR_TRY(launch_update(ctx, g, w, Z0, nullptr, X1, nullptr, pr, 0.f, K, Wl));
             std::swap(X0, X1);
             Z0 = X0;
         }

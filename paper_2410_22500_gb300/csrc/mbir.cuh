@@ -43,19 +43,17 @@ __device__ __forceinline__ float qggmrf_infl(float d, float c0, float inv_tsx, f
     return c0 * r * (1.f + c1 * r);
 }
 
-// SQS update of one (pixel, channel chunk): x+ = max(0, z - g/d) with the data
-// term from the back-projected residual and the qGGMRF prior over the 8 in-plane
+// SQS update of one (pixel, VW values from w0) given bp, the back-projected
+// residual: x+ = max(0, z - g/d) with the qGGMRF prior over the 8 in-plane
 // and (Nr > 1) 2 inter-slice neighbours; with znext, also the momentum point.
 // COH: e, z and xprev were written earlier in the same launch.
-template <int VW, bool COH = false>
-__device__ __forceinline__ void mbir_update_at(const float *__restrict__ e, const float *__restrict__ z,
-                                               const float *__restrict__ xprev, float *__restrict__ xnew,
-                                               float *__restrict__ znext, const ProjTables &t,
-                                               const float *__restrict__ dA, const MbirChan *__restrict__ chp,
-                                               const MbirPrior &pr, float mom_a, int N, int Nc, int Nv, int Nr, int K,
-                                               int Wl, int pix, int w0) {
+template <int VW, bool COH>
+__device__ __forceinline__ void mbir_update_group(const typename VecF<VW>::T &bp, const float *__restrict__ z,
+                                                  const float *__restrict__ xprev, float *__restrict__ xnew,
+                                                  float *__restrict__ znext, const float *__restrict__ dA,
+                                                  const MbirChan *__restrict__ chp, const MbirPrior &pr, float mom_a,
+                                                  int N, int Nc, int Nv, int Nr, int K, int Wl, int pix, int w0) {
     using VF = VecF<VW>;
-    const typename VF::T bp = backproject_at<VW, COH>(e, t, N, Nc, Nv, Wl, pix, w0);
     const int iy = pix / N, ix = pix % N;
     const size_t base = (size_t)pix * Wl + w0;
     const typename VF::T zc = ldv<VW, COH>(z + base);
@@ -124,6 +122,24 @@ __device__ __forceinline__ void mbir_update_at(const float *__restrict__ e, cons
         }
         VF::st(znext + base, zz);
     }
+}
+
+
+// SQS update of one pixel for the G groups of VW values starting at w0: one
+// backward gather (shared table reads), then the update of each group.
+template <int VW, int G, bool COH = false>
+__device__ __forceinline__ void mbir_update_at(const float *__restrict__ e, const float *__restrict__ z,
+                                               const float *__restrict__ xprev, float *__restrict__ xnew,
+                                               float *__restrict__ znext, const ProjTables &t,
+                                               const float *__restrict__ dA, const MbirChan *__restrict__ chp,
+                                               const MbirPrior &pr, float mom_a, int N, int Nc, int Nv, int Nr, int K,
+                                               int Wl, int pix, int w0) {
+    typename VecF<VW>::T bp[G];
+    backproject_at<VW, G, COH>(e, t, N, Nc, Nv, Wl, pix, w0, bp);
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+        mbir_update_group<VW, COH>(bp[g], z, xprev, xnew, znext, dA, chp, pr, mom_a, N, Nc, Nv, Nr, K, Wl, pix,
+                                   w0 + g * VW);
 }
 
 }  // namespace fhr

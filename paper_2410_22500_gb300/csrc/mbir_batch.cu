@@ -89,7 +89,9 @@ __device__ __forceinline__ void batch_forward(const BatchItem &item, const Batch
     if (tid >= sweep * CH) return;
     for (int r = tid / CH; r < item.count; r += sweep) {
         const int row = item.start + r;
-        typename VF::T ax = forward_at<VW, true>(z, P.t, P.N, P.Nc, P.Wl, row, ch * VW);
+        typename VF::T axs[1];
+        forward_at<VW, 1, true>(z, P.t, P.N, P.Nc, P.Wl, row, ch * VW, axs);
+        typename VF::T ax = axs[0];
         const size_t o = (size_t)row * P.Wl + ch * VW;
         const typename VF::T v = VF::ld(P.sino + o);
 #pragma unroll
@@ -106,7 +108,7 @@ __device__ __forceinline__ void batch_update(const BatchItem &item, const BatchP
     const int tid = threadIdx.x, ch = tid % CH;
     if (tid >= sweep * CH) return;
     for (int r = tid / CH; r < item.count; r += sweep)
-        mbir_update_at<VW, true>(P.e, z, xprev, xnew, znext, P.t, P.dA, P.chan, pr, mom, P.N, P.Nc, P.Nv, P.Nr, P.K,
+        mbir_update_at<VW, 1, true>(P.e, z, xprev, xnew, znext, P.t, P.dA, P.chan, pr, mom, P.N, P.Nc, P.Nv, P.Nr, P.K,
                                  P.Wl, item.start + r, ch * VW);
 }
 

@@ -123,34 +123,42 @@ fhr_status proj_build_tables(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &
     return FHR_OK;
 }
 
-// values per channel of the larger of the image and the sinogram
-static size_t slab_values(const fhr_geom *g) {
-    return std::max((size_t)g->N * g->N, (size_t)g->Nv * g->Nc);
+template <template <int, int> class Launch, typename... A>
+static fhr_status gather_dispatch(const GatherShape &s, A... args) {
+    if (s.vw == 4 && s.g == 2) return Launch<4, 2>::run(s, args...);
+    if (s.vw == 4) return Launch<4, 1>::run(s, args...);
+    return Launch<1, 1>::run(s, args...);
 }
+
+template <int VW, int G>
+struct FwdLaunch {
+    static fhr_status run(const GatherShape &s, fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl,
+                          const float *x, float *y, const float *V) {
+        FHR_TIMED(TM_PROJ_FWD, (proj_fwd_kernel<VW, G><<<s.blocks(g->Nv * g->Nc, Wl), s.threads, 0, ctx->stream>>>(
+                                    x, y, V, t, g->N, g->Nc, g->Nv, Wl, s.wc)));
+        return FHR_OK;
+    }
+};
+
+template <int VW, int G>
+struct BwdLaunch {
+    static fhr_status run(const GatherShape &s, fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl,
+                          const float *y, float *x) {
+        FHR_TIMED(TM_PROJ_BWD, (proj_bwd_kernel<VW, G><<<s.blocks(g->N * g->N, Wl), s.threads, 0, ctx->stream>>>(
+                                    y, x, t, g->N, g->Nc, g->Nv, Wl, s.wc)));
+        return FHR_OK;
+    }
+};
 
 fhr_status proj_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *x, float *y,
                         const float *V) {
-    const GatherShape s = gather_shape(Wl, slab_values(g));
-    const unsigned blocks = s.blocks(g->Nv * g->Nc, Wl);
-    if (s.vw == 4)
-        FHR_TIMED(TM_PROJ_FWD, (proj_fwd_kernel<4><<<blocks, s.threads, 0, ctx->stream>>>(x, y, V, t, g->N, g->Nc,
-                                                                                          g->Nv, Wl, s.wc)));
-    else
-        FHR_TIMED(TM_PROJ_FWD, (proj_fwd_kernel<1><<<blocks, s.threads, 0, ctx->stream>>>(x, y, V, t, g->N, g->Nc,
-                                                                                          g->Nv, Wl, s.wc)));
-    return FHR_OK;
+    const GatherShape s = gather_shape(Wl, gather_slab_values(g));
+    return gather_dispatch<FwdLaunch>(s, ctx, g, t, Wl, x, y, V);
 }
 
 fhr_status proj_backward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *y, float *x) {
-    const GatherShape s = gather_shape(Wl, slab_values(g));
-    const unsigned blocks = s.blocks(g->N * g->N, Wl);
-    if (s.vw == 4)
-        FHR_TIMED(TM_PROJ_BWD, (proj_bwd_kernel<4><<<blocks, s.threads, 0, ctx->stream>>>(y, x, t, g->N, g->Nc,
-                                                                                          g->Nv, Wl, s.wc)));
-    else
-        FHR_TIMED(TM_PROJ_BWD, (proj_bwd_kernel<1><<<blocks, s.threads, 0, ctx->stream>>>(y, x, t, g->N, g->Nc,
-                                                                                          g->Nv, Wl, s.wc)));
-    return FHR_OK;
+    const GatherShape s = gather_shape(Wl, gather_slab_values(g));
+    return gather_dispatch<BwdLaunch>(s, ctx, g, t, Wl, y, x);
 }
 
 static size_t proj_ws(const fhr_geom *g, ProjTables *t, void *base) {

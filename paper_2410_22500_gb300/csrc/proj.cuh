@@ -80,10 +80,10 @@ __device__ __forceinline__ typename VecF<VW>::T ldv(const float *p) {
 }
 
 // sum over lines and candidates of A * x[pixel][w] for one ray (item = (v, c)),
-// the VW values w0 .. w0 + VW - 1.
-template <int VW, bool COH = false>
-__device__ __forceinline__ typename VecF<VW>::T forward_at(const float *__restrict__ x, const ProjTables &t, int N,
-                                                           int Nc, int Wl, int item, int w0) {
+// the G groups of VW values starting at w0 (one table read serves all groups).
+template <int VW, int G, bool COH = false>
+__device__ __forceinline__ void forward_at(const float *__restrict__ x, const ProjTables &t, int N, int Nc, int Wl,
+                                           int item, int w0, typename VecF<VW>::T (&acc)[G]) {
     using VF = VecF<VW>;
     const int v = item / Nc, c = item - v * Nc;
     const bool rows = t.rowmaj[v] != 0;
@@ -91,97 +91,127 @@ __device__ __forceinline__ typename VecF<VW>::T forward_at(const float *__restri
     const int *fs = t.fws + (size_t)v * N * Nc + c;
     const int lstride = rows ? N : 1;     // pixel index = l * lstride + q * qstride
     const int qstride = rows ? 1 : N;
-    typename VF::T acc = VF::zero();
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[g] = VF::zero();
     const float *xc = x + w0;
     for (int l = 0; l < N; ++l) {
         const float4 w = __ldg(fw + (size_t)l * Nc);
         const int s0 = __ldg(fs + (size_t)l * Nc);
-        const int p0 = l * lstride + s0 * qstride;
-        if (w.x != 0.f) VF::fma(acc, w.x, ldv<VW, COH>(xc + (size_t)p0 * Wl));
-        if (w.y != 0.f) VF::fma(acc, w.y, ldv<VW, COH>(xc + (size_t)(p0 + qstride) * Wl));
-        if (w.z != 0.f) VF::fma(acc, w.z, ldv<VW, COH>(xc + (size_t)(p0 + 2 * qstride) * Wl));
-        if (w.w != 0.f) VF::fma(acc, w.w, ldv<VW, COH>(xc + (size_t)(p0 + 3 * qstride) * Wl));
+        const float *xp = xc + (size_t)(l * lstride + s0 * qstride) * Wl;
+        const size_t qs = (size_t)qstride * Wl;
+        if (w.x != 0.f) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.x, ldv<VW, COH>(xp + g * VW));
+        }
+        if (w.y != 0.f) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.y, ldv<VW, COH>(xp + qs + g * VW));
+        }
+        if (w.z != 0.f) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.z, ldv<VW, COH>(xp + 2 * qs + g * VW));
+        }
+        if (w.w != 0.f) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.w, ldv<VW, COH>(xp + 3 * qs + g * VW));
+        }
     }
-    return acc;
 }
 
 // Gathers over a vector of Wl values per pixel / ray run in channel chunks of
 // Wc values (Wc | Wl, VW | Wc), chunk-major over the grid: the blocks resident
 // at one time touch one chunk of the image / sinogram, which stays in L2 when
-// the whole does not.  Thread = (item, VW values of the chunk).
+// the whole does not.  Thread = (item, VWG = VW * G consecutive values of the chunk).
 struct GatherIdx {
     int item, w0;
     bool ok;
 };
 
-template <int VW>
+template <int VWG>
 __device__ __forceinline__ GatherIdx gather_idx(int items, int Wl, int Wc) {
-    const int CH = Wc / VW;
+    const int CH = Wc / VWG;
     const int ipb = blockDim.x / CH;
     const int bpc = (items + ipb - 1) / ipb;   // blocks per chunk
     const int chunk = blockIdx.x / bpc;
     GatherIdx r;
     r.item = (blockIdx.x - chunk * bpc) * ipb + threadIdx.x / CH;
-    r.w0 = chunk * Wc + (threadIdx.x % CH) * VW;
+    r.w0 = chunk * Wc + (threadIdx.x % CH) * VWG;
     r.ok = threadIdx.x < ipb * CH && r.item < items && r.w0 < Wl;
     return r;
 }
 
 // y[v][c][w] = sum over lines and candidates of A * x[pixel][w].
 // With V non-null the output is the residual V - A x.
-template <int VW>
-__global__ void __launch_bounds__(1024, 2) proj_fwd_kernel(const float *__restrict__ x, float *__restrict__ y,
+template <int VW, int G>
+__global__ void __launch_bounds__(1024) proj_fwd_kernel(const float *__restrict__ x, float *__restrict__ y,
                                                         const float *__restrict__ V, ProjTables t, int N, int Nc,
                                                         int Nv, int Wl, int Wc) {
     using VF = VecF<VW>;
-    const GatherIdx gi = gather_idx<VW>(Nv * Nc, Wl, Wc);
+    const GatherIdx gi = gather_idx<VW * G>(Nv * Nc, Wl, Wc);
     if (!gi.ok) return;
     const int item = gi.item;
-    typename VF::T acc = forward_at<VW>(x, t, N, Nc, Wl, item, gi.w0);
+    typename VF::T acc[G];
+    forward_at<VW, G>(x, t, N, Nc, Wl, item, gi.w0, acc);
     float *yo = y + (size_t)item * Wl + gi.w0;
-    if (V) {
-        typename VF::T vv = VF::ld(V + (size_t)item * Wl + gi.w0);
 #pragma unroll
-        for (int e = 0; e < VW; ++e) VF::set(acc, e, VF::get(vv, e) - VF::get(acc, e));
+    for (int g = 0; g < G; ++g) {
+        if (V) {
+            typename VF::T vv = VF::ld(V + (size_t)item * Wl + gi.w0 + g * VW);
+#pragma unroll
+            for (int e = 0; e < VW; ++e) VF::set(acc[g], e, VF::get(vv, e) - VF::get(acc[g], e));
+        }
+        VF::st(yo + g * VW, acc[g]);
     }
-    VF::st(yo, acc);
 }
 
-// x[pixel][w] = sum over views and candidate bins of A * y[v][c][w].
-template <int VW, bool COH = false>
-__device__ __forceinline__ typename VecF<VW>::T backproject_at(const float *__restrict__ y, const ProjTables &t, int N,
-                                                               int Nc, int Nv, int Wl, int pix, int w0) {
+// x[pixel][w] = sum over views and candidate bins of A * y[v][c][w], for the
+// G groups of VW values starting at w0.
+template <int VW, int G, bool COH = false>
+__device__ __forceinline__ void backproject_at(const float *__restrict__ y, const ProjTables &t, int N, int Nc,
+                                               int Nv, int Wl, int pix, int w0, typename VecF<VW>::T (&acc)[G]) {
     using VF = VecF<VW>;
-    typename VF::T acc = VF::zero();
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[g] = VF::zero();
     const float *yc = y + w0;
     const size_t NN = (size_t)N * N;
     for (int v = 0; v < Nv; ++v) {
         const float4 w = __ldg(t.bk + v * NN + pix);
-        const size_t row = (size_t)v * Nc + (int)w.w;
-        if (w.x != 0.f) VF::fma(acc, w.x, ldv<VW, COH>(yc + row * Wl));
-        if (w.y != 0.f) VF::fma(acc, w.y, ldv<VW, COH>(yc + (row + 1) * Wl));
-        if (w.z != 0.f) VF::fma(acc, w.z, ldv<VW, COH>(yc + (row + 2) * Wl));
+        const float *yr = yc + ((size_t)v * Nc + (int)w.w) * Wl;
+        if (w.x != 0.f) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.x, ldv<VW, COH>(yr + g * VW));
+        }
+        if (w.y != 0.f) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.y, ldv<VW, COH>(yr + Wl + g * VW));
+        }
+        if (w.z != 0.f) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.z, ldv<VW, COH>(yr + 2 * (size_t)Wl + g * VW));
+        }
     }
-    return acc;
 }
 
-template <int VW>
+template <int VW, int G>
 __global__ void __launch_bounds__(1024) proj_bwd_kernel(const float *__restrict__ y, float *__restrict__ x,
                                                         ProjTables t, int N, int Nc, int Nv, int Wl, int Wc) {
     using VF = VecF<VW>;
-    const GatherIdx gi = gather_idx<VW>(N * N, Wl, Wc);
+    const GatherIdx gi = gather_idx<VW * G>(N * N, Wl, Wc);
     if (!gi.ok) return;
-    VF::st(x + (size_t)gi.item * Wl + gi.w0, backproject_at<VW>(y, t, N, Nc, Nv, Wl, gi.item, gi.w0));
+    typename VF::T acc[G];
+    backproject_at<VW, G>(y, t, N, Nc, Nv, Wl, gi.item, gi.w0, acc);
+#pragma unroll
+    for (int g = 0; g < G; ++g) VF::st(x + (size_t)gi.item * Wl + gi.w0 + g * VW, acc[g]);
 }
 
 // Launch shape for the gathers: chunks of Wc values (the whole vector unless
 // the larger of the image / sinogram slabs exceeds kGatherSlab bytes), CH =
-// Wc / VW threads per item, items per block so that a block holds about
+// Wc / (VW G) threads per item, items per block so that a block holds about
 // `target` threads, and the grid = chunks x blocks per chunk.
 constexpr size_t kGatherSlab = (size_t)32 << 20;
 
 struct GatherShape {
-    int vw, wc, ch, ipb, threads;
+    int vw, g, wc, ch, ipb, threads;   // g: groups of vw values per thread
     unsigned blocks(int items, int Wl) const {
         const int bpc = (items + ipb - 1) / ipb;
         return (unsigned)(bpc * (Wl / wc));
@@ -195,10 +225,18 @@ static inline GatherShape gather_shape(int Wl, size_t slab_values = 0, int targe
     // halve the chunk while the slab of one chunk exceeds the L2 budget (keeping VW | Wc | Wl)
     while (slab_values * (size_t)g.wc * sizeof(float) > kGatherSlab && g.wc % (2 * g.vw) == 0 && g.wc / 2 >= 32)
         g.wc /= 2;
-    g.ch = g.wc / g.vw;
+    // two groups per thread (8 values) share each table read where the chunk allows it;
+    // four (60-64 registers) measured slower on the 128^2 x 64 / K=5 shape
+    g.g = (g.vw == 4 && g.wc % 8 == 0) ? 2 : 1;
+    g.ch = g.wc / (g.vw * g.g);
     g.ipb = std::max(1, target / g.ch);
     g.threads = g.ipb * g.ch;
     return g;
+}
+
+// values per channel of the larger of the image and the sinogram
+static inline size_t gather_slab_values(const fhr_geom *g) {
+    return std::max((size_t)g->N * g->N, (size_t)g->Nv * g->Nc);
 }
 
 size_t proj_tables_bytes(int N, int Nc, int Nv);

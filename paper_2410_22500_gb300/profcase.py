@@ -1,11 +1,17 @@
 """Small, fixed cases for profiling single kernels (ncu captures must stay small).
 
     python -m paper_2410_22500_gb300.profcase nmf_pass [Np]
+    python -m paper_2410_22500_gb300.profcase mbir
 
 `nmf_pass`: P of Np x 1200 uniform f32 (default Np = 92,160: 442 MB, larger than
 L2), K = 5, three fast-HALS iterations from a fixed start.  Launch 0 is the first
 pass; profile with `-k regex:nmf_ -s 1 -c 1` (the tensor-core kernel is
 `nmf_mma_kernel`, the CUDA-core one `nmf_pass_kernel`).
+
+`mbir`: the reconstruction of the 3-D workload's subspace sinograms (N = 128,
+64 slices x K = 5, 90 views x 128 bins; uniform random sinogram), four SQS
+iterations with momentum: launches of proj_fwd_kernel and mbir_update_kernel
+at the benchmark's shapes (profile with `-k regex:"proj_fwd|mbir_update" -s 2 -c 2`).
 """
 import sys
 
@@ -28,9 +34,24 @@ def nmf_pass(Np: int = 92160, Nk: int = 1200, K: int = 5, iters: int = 3) -> Non
     print("ok")
 
 
+def mbir(iters: int = 4) -> None:
+    build.build()
+    ctx = fhr.Context(0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    N, Nr, K, Nv, Nc = 128, 64, 5, 90, 128
+    sino = torch.rand((Nv, Nc, Nr * K), device="cuda", generator=g)
+    ctx.reconstruct(sino, N, Nr, K, iters, momentum=True)
+    torch.cuda.synchronize()
+    ctx.close()
+    print("ok")
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "nmf_pass"
     if case == "nmf_pass":
         nmf_pass(int(sys.argv[2]) if len(sys.argv) > 2 else 92160)
+    elif case == "mbir":
+        mbir()
     else:
         raise SystemExit("unknown case %r" % case)
