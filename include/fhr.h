@@ -264,6 +264,24 @@ fhr_status fhr_fbp(fhr_ctx *ctx, const fhr_geom *geom, int Wl, const float *sino
                    void *ws, size_t ws_bytes);
 
 /* ------------------------------------------------------------------------
+ * Semi-supervised fast material decomposition (Algorithm 2 after the
+ * reconstruction), from the subspace reconstruction and user regions:
+ *   T[i][j] = mean of xs[n][j] over the voxels n with labels[n] == i + 1
+ *             (Eq. trans_mat; labels 0 belong to no region; an empty region
+ *             gives a zero row and status FHR_ERR_ARG in the workspace word),
+ *   xm[n]   = argmin_{x >= 0} || xs[n] - T^T x ||^2 (Eq. mat_recon_nmf; exact
+ *             Lawson-Hanson active sets in FP64, one voxel per thread),
+ *   Dm      = D T^T (Eq. sub_mat_rel_basis).
+ *   xs [Nx][Ns] (the [N][N][Nr*K] volume of fhr_reconstruct is [Nr*N*N][K]),
+ *   labels [Nx] u8, D [Nk][Ns]; out T [Nm][Ns], xm [Nx][Nm], Dm [Nk][Nm]; all
+ *   device, f32.  Ns <= 16, Nm <= min(8, Ns).  Region sums are reduced in a
+ *   fixed order (deterministic).
+ * ---------------------------------------------------------------------- */
+fhr_status fhr_fmd_workspace_size(fhr_ctx *ctx, int64_t Nx, int Ns, int Nm, int Nk, size_t *bytes);
+fhr_status fhr_fmd(fhr_ctx *ctx, int64_t Nx, int Ns, int Nm, int Nk, const float *xs, const uint8_t *labels,
+                   const float *D, float *T, float *xm, float *Dm, void *ws, size_t ws_bytes);
+
+/* ------------------------------------------------------------------------
  * Batched MBIR: Eq. (recon) for every channel and slice of nprob independent
  * problems of uneven size in ONE persistent cooperative launch (replayed from
  * a CUDA graph), two grid-wide phases per iteration (forward residual; fused

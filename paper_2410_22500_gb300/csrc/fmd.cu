@@ -1,0 +1,230 @@
+// Semi-supervised fast material decomposition (Algorithm 2 after the
+// reconstruction), from the subspace reconstruction x^s [Nx][Ns], user
+// region labels and the subspace spectra D^s [Nk][Ns]:
+//   T[i][j] = mean of x^s_{n,j} over region i          (Eq. trans_mat)
+//   x^m_n   = argmin_{x >= 0} || x^s_n - T^T x ||^2     (Eq. mat_recon_nmf)
+//   D^m     = D^s T^T                                   (Eq. sub_mat_rel_basis)
+// Region sums: one block per voxel range, one thread per (region, channel),
+// voxels in order, then a fixed-order sum of the block partials in FP64.  The
+// per-voxel problems: one thread each, Lawson-Hanson active sets on the normal
+// equations (T T^T) x = T x^s_n in FP64 (at most 8 materials).
+#include "common.cuh"
+
+namespace fhr {
+
+constexpr int kFmdMaxM = 8;
+constexpr int kFmdMaxS = 16;
+constexpr int kFmdBlocks = 512;
+
+__global__ void fmd_region_partials(const float *__restrict__ xs, const uint8_t *__restrict__ lab, int64_t Nx, int Ns,
+                                    int Nm, double *part, long long *cnt) {
+    const int t = threadIdx.x;   // (region i, channel j) = (t / Ns, t % Ns)
+    const int i = t / Ns, j = t % Ns;
+    const int64_t per = (Nx + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = min(Nx, (int64_t)blockIdx.x * per), hi = min(Nx, lo + per);
+    double s = 0.0;
+    long long c = 0;
+    if (i < Nm) {
+        for (int64_t n = lo; n < hi; ++n) {
+            if (lab[n] == i + 1) {
+                s += (double)xs[n * Ns + j];
+                ++c;
+            }
+        }
+        part[((size_t)blockIdx.x * Nm + i) * Ns + j] = s;
+        if (j == 0) cnt[(size_t)blockIdx.x * Nm + i] = c;
+    }
+}
+
+// T (FP64 and FP32), the Gram G = T T^T, and a status when a region is empty
+__global__ void fmd_finish(const double *part, const long long *cnt, int nb, int Ns, int Nm, double *T64, float *T,
+                           double *G, int *status) {
+    __shared__ double ts[kFmdMaxM * kFmdMaxS];
+    const int t = threadIdx.x;
+    if (t < Nm * Ns) {
+        const int i = t / Ns, j = t % Ns;
+        double s = 0.0;
+        long long c = 0;
+        for (int b = 0; b < nb; ++b) {
+            s += part[((size_t)b * Nm + i) * Ns + j];
+            c += cnt[(size_t)b * Nm + i];
+        }
+        const double v = c > 0 ? s / (double)c : 0.0;
+        if (c == 0 && j == 0) report(status, FHR_ERR_ARG);
+        ts[t] = v;
+        T64[t] = v;
+        T[t] = (float)v;
+    }
+    __syncthreads();
+    if (t < Nm * Nm) {
+        const int a = t / Nm, b = t % Nm;
+        double g = 0.0;
+        for (int j = 0; j < Ns; ++j) g += ts[a * Ns + j] * ts[b * Ns + j];
+        G[t] = g;
+    }
+}
+
+__global__ void fmd_spectra(const float *__restrict__ D, const double *__restrict__ T64, int Nk, int Ns, int Nm,
+                            float *Dm) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)Nk * Nm) return;
+    const int k = (int)(idx / Nm), i = (int)(idx % Nm);
+    double s = 0.0;
+    for (int j = 0; j < Ns; ++j) s += (double)D[(size_t)k * Ns + j] * T64[i * Ns + j];
+    Dm[idx] = (float)s;
+}
+
+// z_P = G_PP^-1 b_P by Cholesky (FP64), z = 0 outside P; false if not positive definite
+__device__ bool fmd_solve(const double *G, const double *b, int Nm, unsigned P, double *z) {
+    int idx[kFmdMaxM], m = 0;
+    for (int i = 0; i < Nm; ++i)
+        if (P >> i & 1u) idx[m++] = i;
+    double L[kFmdMaxM * kFmdMaxM], y[kFmdMaxM];
+    for (int r = 0; r < m; ++r) {
+        for (int c = 0; c <= r; ++c) {
+            double s = G[idx[r] * Nm + idx[c]];
+            for (int k = 0; k < c; ++k) s -= L[r * kFmdMaxM + k] * L[c * kFmdMaxM + k];
+            if (r == c) {
+                if (!(s > 0.0)) return false;
+                L[r * kFmdMaxM + r] = sqrt(s);
+            } else {
+                L[r * kFmdMaxM + c] = s / L[c * kFmdMaxM + c];
+            }
+        }
+    }
+    for (int r = 0; r < m; ++r) {
+        double s = b[idx[r]];
+        for (int k = 0; k < r; ++k) s -= L[r * kFmdMaxM + k] * y[k];
+        y[r] = s / L[r * kFmdMaxM + r];
+    }
+    for (int i = 0; i < Nm; ++i) z[i] = 0.0;
+    for (int r = m - 1; r >= 0; --r) {
+        double s = y[r];
+        for (int k = r + 1; k < m; ++k) s -= L[k * kFmdMaxM + r] * z[idx[k]];
+        z[idx[r]] = s / L[r * kFmdMaxM + r];
+    }
+    return true;
+}
+
+__global__ void fmd_nnls(const float *__restrict__ xs, const double *__restrict__ T64, const double *__restrict__ Gg,
+                         int64_t Nx, int Ns, int Nm, float *xm) {
+    __shared__ double G[kFmdMaxM * kFmdMaxM], T[kFmdMaxM * kFmdMaxS];
+    for (int i = threadIdx.x; i < Nm * Nm; i += blockDim.x) G[i] = Gg[i];
+    for (int i = threadIdx.x; i < Nm * Ns; i += blockDim.x) T[i] = T64[i];
+    __syncthreads();
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= Nx) return;
+    double b[kFmdMaxM], x[kFmdMaxM], z[kFmdMaxM];
+    double bn = 0.0;
+    for (int i = 0; i < Nm; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < Ns; ++j) s += T[i * Ns + j] * (double)xs[n * Ns + j];
+        b[i] = s;
+        x[i] = 0.0;
+        bn = fmax(bn, fabs(s));
+    }
+    double gmax = 0.0;
+    for (int i = 0; i < Nm * Nm; ++i) gmax = fmax(gmax, fabs(G[i]));
+    const double tol = 1e-13 * fmax(bn, 1e-300) * fmax(1.0, gmax);
+    unsigned P = 0;
+    for (int outer = 0; outer < 3 * kFmdMaxM; ++outer) {
+        // w = b - G x: the most violated coordinate outside P enters
+        int t = -1;
+        double best = tol;
+        for (int i = 0; i < Nm; ++i) {
+            double s = b[i];
+            for (int k = 0; k < Nm; ++k) s -= G[i * Nm + k] * x[k];
+            if (!(P >> i & 1u) && s > best) {
+                best = s;
+                t = i;
+            }
+        }
+        if (t < 0) break;
+        P |= 1u << t;
+        for (int inner = 0; inner < 3 * kFmdMaxM; ++inner) {
+            if (!fmd_solve(G, b, Nm, P, z)) {
+                P &= ~(1u << t);
+                break;
+            }
+            bool feasible = true;
+            for (int i = 0; i < Nm; ++i)
+                if ((P >> i & 1u) && z[i] <= 0.0) feasible = false;
+            if (feasible) {
+                for (int i = 0; i < Nm; ++i) x[i] = z[i];
+                break;
+            }
+            double alpha = 1.0;
+            for (int i = 0; i < Nm; ++i)
+                if ((P >> i & 1u) && z[i] <= 0.0) alpha = fmin(alpha, x[i] / (x[i] - z[i]));
+            for (int i = 0; i < Nm; ++i) {
+                x[i] += alpha * (z[i] - x[i]);
+                if ((P >> i & 1u) && x[i] <= 0.0) {
+                    x[i] = 0.0;
+                    P &= ~(1u << i);
+                }
+            }
+        }
+    }
+    for (int i = 0; i < Nm; ++i) xm[n * Nm + i] = (float)x[i];
+}
+
+struct FmdWs {
+    int *status;
+    double *part, *T64, *G;
+    long long *cnt;
+};
+
+static size_t carve_fmd(void *base, int Ns, int Nm, FmdWs *w) {
+    Carve c(base);
+    FmdWs t;
+    t.status = c.take<int>(kStatusBytes / sizeof(int));
+    t.part = c.take<double>((size_t)kFmdBlocks * Nm * Ns);
+    t.cnt = c.take<long long>((size_t)kFmdBlocks * Nm);
+    t.T64 = c.take<double>((size_t)Nm * Ns);
+    t.G = c.take<double>((size_t)Nm * Nm);
+    if (w) *w = t;
+    return c.size();
+}
+
+static fhr_status check_fmd(fhr_ctx *ctx, int64_t Nx, int Ns, int Nm, int Nk) {
+    FHR_ARG(Nx > 0 && Nk > 0, "Nx and Nk must be positive");
+    FHR_ARG(Ns >= 1 && Ns <= kFmdMaxS, "Ns must be 1..%d", kFmdMaxS);
+    FHR_ARG(Nm >= 1 && Nm <= kFmdMaxM && Nm <= Ns, "Nm must be 1..min(8, Ns)");
+    return FHR_OK;
+}
+
+}  // namespace fhr
+
+using namespace fhr;
+
+extern "C" fhr_status fhr_fmd_workspace_size(fhr_ctx *ctx, int64_t Nx, int Ns, int Nm, int Nk, size_t *bytes) {
+    if (!ctx) return FHR_ERR_ARG;
+    FHR_TRY(check_fmd(ctx, Nx, Ns, Nm, Nk));
+    FHR_ARG(bytes, "bytes is null");
+    *bytes = carve_fmd(nullptr, Ns, Nm, nullptr);
+    return FHR_OK;
+}
+
+extern "C" fhr_status fhr_fmd(fhr_ctx *ctx, int64_t Nx, int Ns, int Nm, int Nk, const float *xs,
+                              const uint8_t *labels, const float *D, float *T, float *xm, float *Dm, void *ws,
+                              size_t ws_bytes) {
+    if (!ctx) return FHR_ERR_ARG;
+    FHR_TRY(check_fmd(ctx, Nx, Ns, Nm, Nk));
+    FHR_ARG(xs && labels && D && T && xm && Dm && ws, "null pointer argument");
+    FHR_ARG(aligned(ws, 256), "workspace must be 256-byte aligned");
+    FmdWs w;
+    const size_t need = carve_fmd(ws, Ns, Nm, &w);
+    FHR_ARG(ws_bytes >= need, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+    FHR_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    FHR_CUDA(cudaMemsetAsync(w.status, 0, kStatusBytes, st));
+    fmd_region_partials<<<kFmdBlocks, kFmdMaxM * kFmdMaxS, 0, st>>>(xs, labels, Nx, Ns, Nm, w.part, w.cnt);
+    FHR_LAUNCHED();
+    fmd_finish<<<1, kFmdMaxM * kFmdMaxS, 0, st>>>(w.part, w.cnt, kFmdBlocks, Ns, Nm, w.T64, T, w.G, w.status);
+    FHR_LAUNCHED();
+    fmd_spectra<<<(unsigned)cdiv((int64_t)Nk * Nm, 256), 256, 0, st>>>(D, w.T64, Nk, Ns, Nm, Dm);
+    FHR_LAUNCHED();
+    fmd_nnls<<<(unsigned)cdiv(Nx, 128), 128, 0, st>>>(xs, w.T64, w.G, Nx, Ns, Nm, xm);
+    FHR_LAUNCHED();
+    return FHR_OK;
+}

@@ -26,7 +26,7 @@ ENTRY_POINTS = (
     "fhr_pipeline_workspace_size", "fhr_pipeline", "fhr_profile_enable", "fhr_profile_read",
     "fhr_decompose_static", "fhr_mlp_workspace_size", "fhr_mlp_forward", "fhr_mlp_grad", "fhr_mlp_adamw",
     "fhr_reconstruct_batch_workspace_size", "fhr_reconstruct_batch", "fhr_reconstruct_batch_autotune",
-    "fhr_fbp_workspace_size", "fhr_fbp", "fhr_io_join",
+    "fhr_fbp_workspace_size", "fhr_fbp", "fhr_io_join", "fhr_fmd_workspace_size", "fhr_fmd",
 )
 
 
@@ -126,6 +126,8 @@ def load():
         L.fhr_reconstruct_batch.argtypes = [vp, ctypes.c_int, PP, BP, vp, sz]
         L.fhr_reconstruct_batch_autotune.argtypes = [vp, ctypes.c_int, PP, BP, vp, sz, ctypes.POINTER(ctypes.c_int)]
         L.fhr_io_join.argtypes = [vp]
+        L.fhr_fmd_workspace_size.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, szp]
+        L.fhr_fmd.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int] + [vp] * 7 + [sz]
         L.fhr_fbp_workspace_size.argtypes = [vp, ctypes.POINTER(Geom), ctypes.c_int, szp]
         L.fhr_fbp.argtypes = [vp, ctypes.POINTER(Geom), ctypes.c_int, vp, vp, vp, sz]
         L.fhr_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -338,6 +340,26 @@ class Context:
             xs = torch.empty((N, N, Wl), dtype=torch.float32, device=sino.device)
         self.check(self.L.fhr_fbp(self._h, ctypes.byref(g), Wl, _ptr(sino), _ptr(xs), _ptr(ws), n.value))
         return xs
+
+    # ------------------------------------------------------------ material decomposition (Algorithm 2)
+    def fmd(self, xs, labels, D, Nm, *, check_status=True):
+        """Semi-supervised FMD: xs [Nx][Ns] (or [N][N][Nr*Ns] viewed so), labels [Nx] u8,
+        D [Nk][Ns] -> (T [Nm][Ns], xm [Nx][Nm], Dm [Nk][Nm])."""
+        torch = _torch()
+        Nk, Ns = D.shape
+        xs2 = xs.reshape(-1, Ns)
+        Nx = xs2.shape[0]
+        n = ctypes.c_size_t()
+        self.check(self.L.fhr_fmd_workspace_size(self._h, Nx, Ns, Nm, Nk, ctypes.byref(n)))
+        ws = self.workspace(n.value)
+        T = torch.empty((Nm, Ns), dtype=torch.float32, device=D.device)
+        xm = torch.empty((Nx, Nm), dtype=torch.float32, device=D.device)
+        Dm = torch.empty((Nk, Nm), dtype=torch.float32, device=D.device)
+        self.check(self.L.fhr_fmd(self._h, Nx, Ns, Nm, Nk, _ptr(xs2), _ptr(labels), _ptr(D), _ptr(T), _ptr(xm),
+                                  _ptr(Dm), _ptr(ws), n.value))
+        if check_status:
+            self.check(self.status(ws))
+        return T, xm, Dm
 
     # ------------------------------------------------------------ batched MBIR
     @staticmethod
