@@ -137,6 +137,141 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
     }
 }
 
+// Layers 1 and 2 with bf16 inputs and bf16 weights on the tensor cores (warp
+// MMA m16n8k16, FP32 accumulation): Act = GELU(A B^T + bias) in bf16 and,
+// when Z is set, the FP32 pre-activation.  A [M][Kd] (row stride lda) and
+// B [N][Kd] (row stride ldb) are both k-contiguous; 128 x 128 tiles, k-steps
+// of 32 through a 4-stage cp.async ring (rows of 64 bytes, 16-byte chunks
+// XOR-swizzled by row so that ldmatrix reads are free of bank conflicts);
+// 8 warps as 2 x 4, a 64 x 32 tile each.  Columns past Kd read as zeros
+// (cp.async zero-fills the part of a chunk beyond its source size).
+constexpr int MBM = 128, MBN = 128, MBK = 32, MST = 4;
+constexpr int kMmaStageBytes = (MBM + MBN) * MBK * 2;
+constexpr int kMmaSmem = MST * kMmaStageBytes;
+
+struct MmaGemmArgs {
+    int M, N, Kd;
+    const __nv_bfloat16 *A;
+    int64_t lda;
+    const __nv_bfloat16 *B;
+    int64_t ldb;
+    const float *bias;
+    float *Z;                 // optional pre-activation [M][ldz]
+    int64_t ldz;
+    __nv_bfloat16 *Act;       // GELU(Z) [M][ldact]
+    int64_t ldact;
+};
+
+__device__ __forceinline__ void mlp_cp16(uint32_t dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void mlp_ldsm4(uint32_t a, uint32_t (&r)[4]) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+__device__ __forceinline__ void mlp_mma(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+                 "{%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// byte offset of 16-byte chunk c (0..3) of tile row r
+__device__ __forceinline__ uint32_t mlp_swz(int r, int c) { return (uint32_t)(r * 64 + ((c ^ ((r >> 1) & 3)) << 4)); }
+
+__global__ void __launch_bounds__(256, 2) mlp_gemm_mma(MmaGemmArgs g) {
+    extern __shared__ __align__(128) unsigned char mlp_sm[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 2, wn = warp & 3;
+    const int64_t m0 = (int64_t)blockIdx.y * MBM;
+    const int n0 = blockIdx.x * MBN;
+    const int nk = (g.Kd + MBK - 1) / MBK;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(mlp_sm);
+
+    auto load = [&](int kt, int st) {
+        const uint32_t sa = sbase + st * kMmaStageBytes, sb = sa + MBM * MBK * 2;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int idx = tid + e * 256;
+            const int r = idx >> 2, c = idx & 3;
+            const int k = kt * MBK + c * 8;
+            const int kb = min(16, max(0, (g.Kd - k) * 2));
+            const int64_t ga = m0 + r;
+            const bool ra = ga < g.M && kb > 0;
+            mlp_cp16(sa + mlp_swz(r, c), g.A + (ra ? ga * g.lda + k : 0), ra ? kb : 0);
+            const int gb = n0 + r;
+            const bool rb = gb < g.N && kb > 0;
+            mlp_cp16(sb + mlp_swz(r, c), g.B + (rb ? (int64_t)gb * g.ldb + k : 0), rb ? kb : 0);
+        }
+    };
+
+    float acc[4][4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+
+#pragma unroll
+    for (int st = 0; st < MST - 1; ++st) {
+        if (st < nk) load(st, st);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int kt = 0; kt < nk; ++kt) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(MST - 2) : "memory");
+        __syncthreads();
+        if (kt + MST - 1 < nk) load(kt + MST - 1, (kt + MST - 1) % MST);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        const uint32_t sa = sbase + (kt % MST) * kMmaStageBytes, sb = sa + MBM * MBK * 2;
+#pragma unroll
+        for (int kk = 0; kk < MBK / 16; ++kk) {
+            uint32_t af[4][4], bq[2][4];
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi)
+                mlp_ldsm4(sa + mlp_swz(wm * 64 + mi * 16 + (lane & 15), kk * 2 + (lane >> 4)), af[mi]);
+#pragma unroll
+            for (int nj = 0; nj < 2; ++nj)
+                mlp_ldsm4(sb + mlp_swz(wn * 32 + nj * 16 + (lane & 7) + ((lane >> 4) << 3), kk * 2 + ((lane >> 3) & 1)),
+                          bq[nj]);
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni)
+                    mlp_mma(acc[mi][ni], af[mi], bq[ni >> 1][(ni & 1) * 2], bq[ni >> 1][(ni & 1) * 2 + 1]);
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+
+    const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int ni = 0; ni < 4; ++ni) {
+        const int col = n0 + wn * 32 + ni * 8 + 2 * tq;
+        if (col >= g.N) continue;   // N is a multiple of 8: col + 1 < N as well
+        const float b0 = g.bias[col], b1 = g.bias[col + 1];
+#pragma unroll
+        for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t row = m0 + wm * 64 + mi * 16 + gq + 8 * h;
+                if (row >= g.M) continue;
+                const float z0 = acc[mi][ni][2 * h] + b0, z1 = acc[mi][ni][2 * h + 1] + b1;
+                if (g.Z) *reinterpret_cast<float2 *>(g.Z + row * g.ldz + col) = make_float2(z0, z1);
+                *reinterpret_cast<__nv_bfloat162 *>(g.Act + row * g.ldact + col) =
+                    __floats2bfloat162_rn(gelu_f(z0), gelu_f(z1));
+            }
+    }
+}
+
+// bf16 copy of a [rows][cols] f32 weight block with rows padded to ld (zeros)
+__global__ void pad_bf16_kernel(const float *w, int rows, int cols, int ld, __nv_bfloat16 *out) {
+    const int64_t n = (int64_t)rows * ld;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / ld), c = (int)(i % ld);
+        out[i] = __float2bfloat16_rn(c < cols ? w[(int64_t)r * cols + c] : 0.f);
+    }
+}
+
 // loss partials and dZ3 = 2/(M K) (y - t) sigmoid(z3), one thread per output
 __global__ void mlp_loss_kernel(const float *Y, const float *Z3, const float *T, int64_t n, float scale, float *dZ3,
                                 double *part) {
@@ -224,12 +359,14 @@ static MlpLayout mlp_layout(const fhr_mlp_dims *d) {
     return L;
 }
 
-constexpr int kMlpChunk = 32768;      // pixel rows per forward/backward chunk
+constexpr int kMlpChunk = 32768;      // pixel rows per training (forward + backward) chunk
+constexpr int kMlpFwdChunk = 65536;   // pixel rows per inference chunk
 constexpr int kSplitRows = 2048;      // contraction rows per split of a weight gradient
 
 struct MlpWs {
     int *status;
     __nv_bfloat16 *wb;      // bf16 weights (packed like the params) or null
+    __nv_bfloat16 *wp1, *wp2;   // bf16 W1, W2 with rows padded to a multiple of 8 (tensor-core layers)
     float *Z1, *Z2, *Z3, *Y;
     void *A1, *A2;
     float *dZ3, *dZ2, *dZ1;
@@ -239,19 +376,26 @@ struct MlpWs {
 };
 
 static int64_t mlp_splits(int64_t M) { return cdiv(M, kSplitRows); }
+static int pad8(int n) { return (n + 7) / 8 * 8; }
 
 static size_t carve_mlp(void *base, const fhr_mlp_dims *d, int train, MlpWs *w) {
     const MlpLayout L = mlp_layout(d);
-    const int64_t R = kMlpChunk;
+    const int64_t R = train ? kMlpChunk : kMlpFwdChunk;
     const int es = d->weights_bf16 ? 2 : 4;
     Carve c(base);
     MlpWs t{};
     t.status = c.take<int>(kStatusBytes / sizeof(int));
     t.wb = d->weights_bf16 ? c.take<__nv_bfloat16>((size_t)L.n) : nullptr;
-    t.Z1 = c.take<float>((size_t)R * d->H1);
-    t.Z2 = c.take<float>((size_t)R * d->H2);
-    t.Z3 = c.take<float>((size_t)R * d->K);
-    t.Y = c.take<float>((size_t)R * d->K);
+    if (d->weights_bf16) {
+        t.wp1 = c.take<__nv_bfloat16>((size_t)d->H1 * pad8(d->Nk));
+        t.wp2 = c.take<__nv_bfloat16>((size_t)d->H2 * pad8(d->H1));
+    }
+    if (train) {   // pre-activations, kept for the backward pass
+        t.Z1 = c.take<float>((size_t)R * d->H1);
+        t.Z2 = c.take<float>((size_t)R * d->H2);
+        t.Z3 = c.take<float>((size_t)R * d->K);
+        t.Y = c.take<float>((size_t)R * d->K);
+    }
     t.A1 = c.take<char>((size_t)R * d->H1 * es);
     t.A2 = c.take<char>((size_t)R * d->H2 * es);
     if (train) {
@@ -290,17 +434,56 @@ static const void *wptr(const float *prm, const MlpWs &w, int64_t off) {
     return prm + off;
 }
 
-// forward of `rows` pixel rows starting at X (row stride ldx); fills Z1..Y
+// the tensor-core layers take bf16 rows and weights with 16-byte aligned rows
+static bool mma_layers(const fhr_mlp_dims *d, const void *X) {
+    return d->x_dtype == FHR_BF16 && d->weights_bf16 && d->ldx % 8 == 0 && d->H1 % 8 == 0 && d->H2 % 8 == 0 &&
+           ((uintptr_t)X & 15) == 0;
+}
+
+static fhr_status mma_layer(fhr_ctx *ctx, const MmaGemmArgs &g) {
+    FHR_CUDA(cudaFuncSetAttribute(mlp_gemm_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kMmaSmem));
+    dim3 grid((unsigned)cdiv(g.N, MBN), (unsigned)cdiv(g.M, MBM));
+    mlp_gemm_mma<<<grid, 256, kMmaSmem, ctx->stream>>>(g);
+    FHR_LAUNCHED();
+    return FHR_OK;
+}
+
+// forward of `rows` pixel rows starting at X (row stride ldx); fills A1, A2,
+// Yout (and Z1, Z2, Z3out when the pre-activations are wanted for a backward pass)
 template <typename TX, typename TW>
 static fhr_status forward_chunk(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *prm, const MlpWs &w, int64_t rows,
-                                const void *X, float *Yout, float *Z3out) {
+                                const void *X, float *Yout, float *Z3out, bool need_z) {
     const MlpLayout L = mlp_layout(d);
+    if (sizeof(TX) == 2 && sizeof(TW) == 2 && mma_layers(d, X)) {
+        MmaGemmArgs m{};
+        m.M = (int)rows; m.N = d->H1; m.Kd = d->Nk;
+        m.A = (const __nv_bfloat16 *)X; m.lda = d->ldx;
+        m.B = w.wp1; m.ldb = pad8(d->Nk);
+        m.bias = prm + L.ob1;
+        m.Z = need_z ? w.Z1 : nullptr; m.ldz = d->H1;
+        m.Act = (__nv_bfloat16 *)w.A1; m.ldact = d->H1;
+        FHR_TRY(mma_layer(ctx, m));
+        m.N = d->H2; m.Kd = d->H1;
+        m.A = (const __nv_bfloat16 *)w.A1; m.lda = d->H1;
+        m.B = w.wp2; m.ldb = pad8(d->H1);
+        m.bias = prm + L.ob2;
+        m.Z = need_z ? w.Z2 : nullptr; m.ldz = d->H2;
+        m.Act = (__nv_bfloat16 *)w.A2; m.ldact = d->H2;
+        FHR_TRY(mma_layer(ctx, m));
+        GemmArgs g{};
+        g.M = (int)rows; g.N = d->K; g.Kd = d->H2;
+        g.A = w.A2; g.sai = d->H2; g.sak = 1;
+        g.B = wptr<TW>(prm, w, L.oW3); g.sbk = 1; g.sbj = d->H2;
+        g.C = Yout; g.ldc = d->K; g.C2 = Z3out; g.ldc2 = d->K;
+        g.bias = prm + L.ob3; g.kchunk = g.Kd;
+        return gemm<TW, TW, EPI_BIAS_SOFTPLUS>(ctx, g);
+    }
     GemmArgs g{};
     // layer 1: Z1 = X W1^T + b1
     g.M = (int)rows; g.N = d->H1; g.Kd = d->Nk;
     g.A = X; g.sai = d->ldx; g.sak = 1;
     g.B = wptr<TW>(prm, w, L.oW1); g.sbk = 1; g.sbj = d->Nk;
-    g.C = w.Z1; g.ldc = d->H1;
+    g.C = need_z ? w.Z1 : nullptr; g.ldc = d->H1;
     g.C2 = w.A1; g.c2_bf16 = sizeof(TW) == 2; g.ldc2 = d->H1;
     g.bias = prm + L.ob1; g.kchunk = g.Kd;
     FHR_TRY((gemm<TX, TW, EPI_BIAS_GELU>(ctx, g)));
@@ -308,7 +491,7 @@ static fhr_status forward_chunk(fhr_ctx *ctx, const fhr_mlp_dims *d, const float
     g.N = d->H2; g.Kd = d->H1;
     g.A = w.A1; g.sai = d->H1;
     g.B = wptr<TW>(prm, w, L.oW2); g.sbj = d->H1;
-    g.C = w.Z2; g.ldc = d->H2; g.C2 = w.A2; g.ldc2 = d->H2;
+    g.C = need_z ? w.Z2 : nullptr; g.ldc = d->H2; g.C2 = w.A2; g.ldc2 = d->H2;
     g.bias = prm + L.ob2; g.kchunk = g.Kd;
     FHR_TRY((gemm<TW, TW, EPI_BIAS_GELU>(ctx, g)));
     // layer 3: Y = softplus(A2 W3^T + b3)
@@ -393,6 +576,12 @@ static fhr_status prep_weights(fhr_ctx *ctx, const fhr_mlp_dims *d, const float 
     const MlpLayout L = mlp_layout(d);
     to_bf16_kernel<<<(unsigned)std::min<int64_t>(cdiv(L.n, 256), 4096), 256, 0, ctx->stream>>>(prm, L.n, w.wb);
     FHR_LAUNCHED();
+    pad_bf16_kernel<<<(unsigned)std::min<int64_t>(cdiv((int64_t)d->H1 * pad8(d->Nk), 256), 4096), 256, 0,
+                      ctx->stream>>>(prm + L.oW1, d->H1, d->Nk, pad8(d->Nk), w.wp1);
+    FHR_LAUNCHED();
+    pad_bf16_kernel<<<(unsigned)std::min<int64_t>(cdiv((int64_t)d->H2 * pad8(d->H1), 256), 4096), 256, 0,
+                      ctx->stream>>>(prm + L.oW2, d->H2, d->H1, pad8(d->H1), w.wp2);
+    FHR_LAUNCHED();
     return FHR_OK;
 }
 
@@ -400,10 +589,10 @@ template <typename TX, typename TW>
 static fhr_status forward_all(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *prm, const MlpWs &w, int64_t M,
                               const void *X, float *Y) {
     const int es = d->x_dtype == FHR_BF16 ? 2 : 4;
-    for (int64_t r0 = 0; r0 < M; r0 += kMlpChunk) {
-        const int64_t rows = std::min<int64_t>(kMlpChunk, M - r0);
+    for (int64_t r0 = 0; r0 < M; r0 += kMlpFwdChunk) {
+        const int64_t rows = std::min<int64_t>(kMlpFwdChunk, M - r0);
         FHR_TRY((forward_chunk<TX, TW>(ctx, d, prm, w, rows, (const char *)X + r0 * d->ldx * es, Y + r0 * d->K,
-                                       w.Z3)));
+                                       nullptr, false)));
     }
     return FHR_OK;
 }
@@ -417,13 +606,18 @@ fhr_status mlp_forward_impl(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *pr
     const size_t need = carve_mlp(ws, d, 0, &w);
     FHR_ARG(ws_bytes >= need, "workspace too small: %zu < %zu bytes", ws_bytes, need);
     FHR_CUDA(cudaSetDevice(ctx->device));
-    FHR_TRY(prep_weights(ctx, d, prm, w));
-    if (d->x_dtype == FHR_BF16) {
-        if (d->weights_bf16) return forward_all<__nv_bfloat16, __nv_bfloat16>(ctx, d, prm, w, M, X, Y);
-        return forward_all<__nv_bfloat16, float>(ctx, d, prm, w, M, X, Y);
+    cudaEvent_t *ev = timer_begin(ctx, TM_MLP_FORWARD);   // the whole forward, when profiling
+    fhr_status s = prep_weights(ctx, d, prm, w);
+    if (s == FHR_OK) {
+        if (d->x_dtype == FHR_BF16)
+            s = d->weights_bf16 ? forward_all<__nv_bfloat16, __nv_bfloat16>(ctx, d, prm, w, M, X, Y)
+                                : forward_all<__nv_bfloat16, float>(ctx, d, prm, w, M, X, Y);
+        else
+            s = d->weights_bf16 ? forward_all<float, __nv_bfloat16>(ctx, d, prm, w, M, X, Y)
+                                : forward_all<float, float>(ctx, d, prm, w, M, X, Y);
     }
-    if (d->weights_bf16) return forward_all<float, __nv_bfloat16>(ctx, d, prm, w, M, X, Y);
-    return forward_all<float, float>(ctx, d, prm, w, M, X, Y);
+    if (ev) cudaEventRecord(ev[1], ctx->stream);
+    return s;
 }
 
 size_t mlp_ws_bytes(const fhr_mlp_dims *d, int train) { return carve_mlp(nullptr, d, train, nullptr); }
@@ -432,7 +626,7 @@ template <typename TX, typename TW>
 static fhr_status grad_impl(fhr_ctx *ctx, const fhr_mlp_dims *d, const float *prm, const MlpWs &w, int64_t M,
                             const void *X, const float *T, float *grad, double *loss) {
     FHR_ARG(M > 0 && M <= kMlpChunk, "fhr_mlp_grad takes 1..%d rows per call", kMlpChunk);
-    FHR_TRY((forward_chunk<TX, TW>(ctx, d, prm, w, M, X, w.Y, w.Z3)));
+    FHR_TRY((forward_chunk<TX, TW>(ctx, d, prm, w, M, X, w.Y, w.Z3, true)));
     const int64_t n = M * d->K;
     const int nb = (int)std::min<int64_t>(cdiv(n, 256), 1024);
     mlp_loss_kernel<<<nb, 256, 0, ctx->stream>>>(w.Y, w.Z3, T, n, 2.f / (float)n, w.dZ3, w.lpart);

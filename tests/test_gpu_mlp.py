@@ -51,6 +51,50 @@ def test_forward_bf16_weights_and_rows(fx, orc):
     assert err <= 2e-2
 
 
+def test_forward_tensor_core_layers_at_the_volume_shape(fx, orc):
+    # the 1500 -> 256 -> 128 -> 6 network on bf16 rows of stride 1504 (the tensor-core layers),
+    # two inference chunks with a ragged tail: FP64 oracle on sampled rows, and the CUDA-core
+    # layers (taken for a row stride that is not a multiple of 8) on all rows
+    import torch
+
+    rng = np.random.default_rng(21)
+    dims = (1500, 256, 128, 6)
+    prm = _params(rng, dims)
+    M = 70001
+    X = torch.rand((M, 1504), generator=torch.Generator().manual_seed(3)).mul_(2).to(torch.bfloat16)
+    p32 = torch.from_numpy(prm.astype(np.float32)).cuda()
+    d = fx.mlp_dims(*dims, ldx=1504, x_bf16=True, weights_bf16=True)
+    Y = fx.mlp_forward(d, p32, X.cuda()).cpu().numpy()
+    rows = np.sort(rng.choice(M, 600, replace=False))
+    rows[-1] = M - 1
+    ref = orc.mlp_forward(prm, X[rows, :1500].float().numpy().astype(np.float64), dims)
+    err = _rel(Y[rows], ref)
+    print("tensor-core forward: relative error %.2e vs FP64" % err)
+    assert err <= 2e-2
+    X2 = torch.zeros((M, 1502), dtype=torch.bfloat16)
+    X2[:, :1500] = X[:, :1500]
+    d2 = fx.mlp_dims(*dims, ldx=1502, x_bf16=True, weights_bf16=True)
+    Y2 = fx.mlp_forward(d2, p32, X2.cuda()).cpu().numpy()
+    assert _rel(Y, Y2) <= 2e-3
+
+
+def test_gradient_bf16_rows_and_weights(fx, orc):
+    # the training forward on the tensor-core layers (pre-activations kept) and the backward
+    import torch
+
+    rng = np.random.default_rng(9)
+    dims = (72, 40, 24, 3)
+    M = 3000
+    prm = _params(rng, dims, scale=1.5)
+    X = torch.from_numpy(rng.uniform(0, 1.5, size=(M, 72)).astype(np.float32)).to(torch.bfloat16)
+    T = rng.uniform(0.1, 1.0, size=(M, 3)).astype(np.float32)
+    d = fx.mlp_dims(*dims, x_bf16=True, weights_bf16=True)
+    loss, g = fx.mlp_grad(d, torch.from_numpy(prm.astype(np.float32)).cuda(), X.cuda(), torch.from_numpy(T).cuda())
+    lref, gref = orc.mlp_grad(prm, X.float().numpy().astype(np.float64), T.astype(np.float64), dims)
+    assert abs(float(loss.item()) - lref) <= 2e-2 * lref
+    assert _rel(g.cpu().numpy(), gref) <= 5e-2
+
+
 @pytest.mark.parametrize("M,dims", [(200, (30, 24, 12, 3)), (1500, (64, 48, 20, 5))])
 def test_gradient_matches_oracle(fx, orc, M, dims):
     import torch
