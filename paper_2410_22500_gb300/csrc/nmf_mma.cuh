@@ -15,8 +15,8 @@
 //                   for the whole launch;
 //   2 update warps  (alternate tiles) sum the 13 partials of r, run the HALS
 //                   V half-step of the 8 pixels and write W; they stage w
-//                   for phase 3, where consumer warp 0 also adds w^T w to G_W
-//                   with two more MMAs.
+//                   for phase 3 and add w^T w to G_W from the staged
+//                   fragments with two MMAs (so the consumers' work is even).
 // The update warps and the producer sit on one SM sub-partition with a single
 // consumer warp (warps w and w + 4k share one), since the update is
 // latency-bound; with LAG = 2 its latency is off the per-tile critical path.
@@ -44,7 +44,7 @@ __host__ __device__ inline int mma_nkw(int ldP) {
 }
 
 struct MmaSmem {
-    size_t tiles, wst, wb, red, gsm, invd, wsc, ssq, bars, total;
+    size_t tiles, wst, wb, red, gsm, invd, wsc, ssq, gwx, bars, total;
     uint32_t rs;   // bytes per staged pixel row
 };
 
@@ -68,6 +68,7 @@ __host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stage
     L.invd = take((size_t)kMaxK * sizeof(float), 16);
     L.wsc = take((size_t)kMaxK * sizeof(float), 16);
     L.ssq = take((size_t)kMmaCW * sizeof(float), 16);
+    L.gwx = take((size_t)2 * 32 * 4 * sizeof(float), 16);    // G_W fragments of the two update warps
     L.bars = take((size_t)(2 * stages + 2 * nb) * sizeof(uint64_t), 8);
     L.total = (o + 127) / 128 * 128;
     return L;
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     float *invd = reinterpret_cast<float *>(smem + Lyt.invd);
     float *wsc = reinterpret_cast<float *>(smem + Lyt.wsc);
     float *ssqs = reinterpret_cast<float *>(smem + Lyt.ssq);
+    float *gwx = reinterpret_cast<float *>(smem + Lyt.gwx);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + Lyt.bars);
     uint64_t *empty = full + S;
     uint64_t *redfull = empty + S;
@@ -285,6 +287,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
         // lane = (row, group of 4 partial sums)
         const int uw = warp;   // 0 or 1
         const int row = lane >> 2, grp = lane & 3;
+        const int lmat = lane >> 3;
+        float gw[4] = {0.f, 0.f, 0.f, 0.f};   // G_W of this warp's tiles (rows s and s + 8 of the accumulator)
         // G (constant for the launch): upper triangle in registers
         float gu[kMaxK * (kMaxK + 1) / 2];
         {
@@ -414,9 +418,43 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 }
             }
             __syncwarp();
+            // G_W += w^T w on the tensor cores, from the staged fragments (read before the
+            // hand-off releases the buffer):
+            // f32  A = [w_big^T; w_small^T] (rows 0..7; 8..15), B = w_big, then A = w_big^T, B = w_small;
+            // bf16 A = [w_hi^T | w_lo^T] along k, B = [w_hi; w_hi], then A = w_hi^T, B = w_lo
+            uint32_t wB0, wB1, wS0, wS1;
+            if (F32) {
+                ldsm_x4(wbb + (uint32_t)((lmat >> 1) * 8 * kMmaWbStride + (lane & 7) * kMmaWbStride + (lmat & 1) * 16),
+                        wB0, wB1, wS0, wS1);
+            } else {
+                ldsm_x2(wbb + (uint32_t)((lmat & 1) * 8 * kMmaWbStride + (lane & 7) * kMmaWbStride), wB0, wS0);
+                wB1 = wS1 = 0u;
+            }
+            __syncwarp();
             if (lane == 0) mbar_arrive(&wready[b]);
+            if (F32) {
+                mma_tf32(gw, wB0, wS0, wB1, wS1, wB0, wB1);
+                mma_tf32(gw, wB0, 0u, wB1, 0u, wS0, wS1);
+            } else {
+                mma_bf16(gw, wB0, 0u, wS0, 0u, wB0, wB0);
+                mma_bf16(gw, wB0, 0u, 0u, 0u, wS0, 0u);
+            }
         }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) gwx[(uw * 32 + lane) * 4 + e] = gw[e];
         bar_sync(1, NT + 64);
+        if (uw == 0) {
+            // G_W[s][t]: accumulator rows s (high part) and s + 8 (low part), column t
+            const int g = lane >> 2, tig = lane & 3;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int t = 2 * tig + e;
+                float v = 0.f;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) v += gwx[(u * 32 + lane) * 4 + e] + gwx[(u * 32 + lane) * 4 + 2 + e];
+                if (g < K && t < K) a.Gpart[(size_t)blockIdx.x * K * K + g * K + t] = v;
+            }
+        }
         if (uw == 0 && lane == 0 && a.want_ssq) {
             float acc = 0.f;
             for (int wp = 0; wp < kMmaCW; ++wp) acc += ssqs[wp];
@@ -462,7 +500,6 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) Q[m][e] = 0.f;
     float ssq = 0.f;
-    float gw[4] = {0.f, 0.f, 0.f, 0.f};   // warp 0: G_W (rows s and s + 8 of the accumulator)
     bool ok = true;
     int s_cur = 0, s3 = 0;            // stages of the tiles in phase 1 and in phase 3
     uint32_t par_cur = 0;
@@ -576,18 +613,6 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 wB1 = 0u;
                 wS1 = 0u;
             }
-            if (warp == 0) {
-                // G_W += w^T w on the tensor cores from the same fragments:
-                // f32  A = [w_big^T; w_small^T] (rows 0..7; 8..15), B = w_big, then A = w_big^T, B = w_small;
-                // bf16 A = [w_hi^T | w_lo^T] along k, B = [w_hi; w_hi], then A = w_hi^T, B = w_lo
-                if (F32) {
-                    mma_tf32(gw, wB0, wS0, wB1, wS1, wB0, wB1);
-                    mma_tf32(gw, wB0, 0u, wB1, 0u, wS0, wS1);
-                } else {
-                    mma_bf16(gw, wB0, 0u, wS0, 0u, wB0, wB0);
-                    mma_bf16(gw, wB0, 0u, 0u, 0u, wS0, 0u);
-                }
-            }
 #pragma unroll
             for (int m = 0; m < MB; ++m) {
                 const int m0 = c0 + m * 16;
@@ -634,14 +659,6 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
             const int k = c0 + m * 16 + (F32 ? 2 * g + (e >> 1) : g + (e >> 1) * 8);
             const int s = 2 * tig + (e & 1);
             if (k < a.Nk && s < K) a.Qpart[((size_t)blockIdx.x * a.Nk + k) * K + s] = Q[m][e];
-        }
-    }
-    if (warp == 0) {
-        // G_W[s][t]: accumulator rows s (high part) and s + 8 (low part), column t
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int t = 2 * tig + e;
-            if (g < K && t < K) a.Gpart[(size_t)blockIdx.x * K * K + g * K + t] = gw[e] + gw[2 + e];
         }
     }
 #pragma unroll
