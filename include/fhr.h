@@ -371,9 +371,11 @@ fhr_status fhr_mlp_adamw(fhr_ctx *ctx, int64_t n, float *params, const float *gr
  * staging buffers in the workspace, with asynchronous copies on the
  * context's stream (pinned host memory makes them truly asynchronous).
  * bg_mask, dead_bins are device pointers or NULL.  D_out [Nk][K] device
- * float, obj device double [nmf.iters] or NULL.  nmf.init must be
- * FHR_INIT_NNDSVD (the pipeline has no starting point of its own).  The
- * reconstruction starts from x^s = 0.  Sizes in norm, nmf, geom and mbir
+ * float, obj device double [nmf.iters] or NULL.  nmf.init is
+ * FHR_INIT_NNDSVD, FHR_INIT_CLUSTER or FHR_INIT_LEARNED (nmf.mlp with
+ * ldx = norm.ldP and x_dtype = norm.p_dtype); FHR_INIT_GIVEN is rejected, the
+ * pipeline having no starting point of its own.  The reconstruction starts
+ * from x^s = 0.  Sizes in norm, nmf, geom and mbir
  * must agree (Np = Nv*Nr*Nc, geom.Nr = norm.Nr, mbir.K = nmf.K).
  * ---------------------------------------------------------------------- */
 typedef struct {

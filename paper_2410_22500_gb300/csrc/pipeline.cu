@@ -48,8 +48,8 @@ static fhr_status pipe_check(fhr_ctx *ctx, const fhr_pipeline_params *p) {
     FHR_ARG(p->nmf.Nk == n.Nk && p->nmf.ldP == n.ldP && p->nmf.p_dtype == n.p_dtype, "norm and nmf disagree");
     FHR_ARG(p->geom.Nr == n.Nr && p->geom.Nc == n.Nc && p->geom.Nv == n.Nv, "geometry and counts disagree");
     FHR_ARG(p->mbir.K == p->nmf.K, "mbir.K != nmf.K");
-    FHR_ARG(p->nmf.init == FHR_INIT_NNDSVD || p->nmf.init == FHR_INIT_CLUSTER,
-            "the pipeline starts the decomposition from NNDSVD or the clustering start");
+    FHR_ARG(p->nmf.init == FHR_INIT_NNDSVD || p->nmf.init == FHR_INIT_CLUSTER || p->nmf.init == FHR_INIT_LEARNED,
+            "the pipeline starts the decomposition from NNDSVD, the clustering start or the learned start");
     FHR_ARG(p->xh_dtype == FHR_F32 || p->xh_dtype == FHR_BF16, "bad xh_dtype");
     FHR_ARG(p->recon == FHR_RECON_MBIR || p->recon == FHR_RECON_FBP, "bad recon");
     return FHR_OK;

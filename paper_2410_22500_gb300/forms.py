@@ -3,6 +3,7 @@ line per case; device timing with CUDA events on the library's stream).
 
     python -m paper_2410_22500_gb300.forms precision
     python -m paper_2410_22500_gb300.forms batched [n_problems] [iters]
+    python -m paper_2410_22500_gb300.forms learned [n_train]
 
 `precision`: the 256^3 volume (6 ellipsoids, Nk = 1500, 120 views, 256 x 256
 detector, 100 counts per bin; P is 7.86M x 1500) through Algorithm 1 with P
@@ -17,7 +18,23 @@ library's projector from seeded disk phantoms.  Times the batched
 reconstruction (one persistent launch, autotuned work-item size) against one
 fhr_reconstruct call per problem, both including their set-up, and reports the
 per-problem times of the latter.
+
+`learned`: the learned warm start with BF16 P against the plain FP32 form.
+A 1500 -> 256 -> 128 -> 6 MLP (GELU, GELU, softplus; BF16 weights in the
+forward, FP32 accumulation) is trained by the library's kernels on the plain
+method's coefficients for n_train (default 12) seeded 128x128x32 phantoms
+(120 views, 128 x 32 detector, 50 counts/bin; 131072 sampled pixel rows each)
+whose six materials share one spectra library.  A held-out 256x256x128 volume
+(Nk = 1500, 120 views, 256 x 128 detector, 50 counts/bin) is then run through
+Algorithm 1 twice: the plain FP32 form (NNDSVD start, 200 iterations) and the
+learned + BF16 form with the fewest iterations whose factors reach the plain
+final objective within 1e-3 relative, both objectives evaluated against the
+FP32 P.  Reports iterations, whole-pipeline times and the speedup; also the
+plain form stopped at the iteration where it first came within 1e-3 of its own
+final objective, and the BF16 form from the NNDSVD start with the fewest
+iterations that reach the same target (what the learned start adds to BF16).
 """
+import ctypes
 import json
 import sys
 
@@ -127,10 +144,148 @@ def batched(n_problems: int = 40, iters: int = 100) -> None:
     ctx.close()
 
 
+def _objective(P, Nk, D, W, rows=131072):
+    """||P - W D^T||_F^2 against the FP32 P, FP64 accumulation (evaluation only)."""
+    tot = 0.0
+    for r0 in range(0, P.shape[0], rows):
+        R = P[r0:r0 + rows, :Nk].float() - W[r0:r0 + rows] @ D.T
+        tot += float((R.double() ** 2).sum().item())
+    return tot
+
+
+def _first_within(obj, target):
+    hit = np.nonzero(np.asarray(obj) <= target)[0]
+    return int(hit[0]) + 1 if len(hit) else None
+
+
+def learned(n_train: int = 12) -> None:
+    from . import learned as lw
+
+    build.build()
+    torch.backends.cuda.matmul.allow_tf32 = False
+    ctx = fhr.Context(0)
+    Nk, K, H1, H2, iters = 1500, 6, 256, 128, 200
+    lib = synth.spectra_library(Nk, K, seed=77)
+    ldb = (Nk + 7) // 8 * 8
+    # training set: plain-method coefficients on the BF16 P of small phantoms
+    Xs, Ts = [], []
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    for i in range(n_train):
+        pb = synth.make_problem(N=128, Nr=32, Nc=128, Nv=120, Nk=Nk, Nm=K, I0=50, seed=5000 + i, spectra=lib,
+                                three_d=True)
+        y, y0 = synth.counts_torch(pb, device="cuda")
+        Pb = ctx.normalise(y, y0, p_dtype=fhr.BF16)
+        D, W, _ = ctx.decompose(Pb, Nk, K, iters, init=fhr.INIT_NNDSVD, obj=False)
+        perm = torch.as_tensor(lw.match_order(D.cpu().numpy(), lib), device="cuda")
+        idx = torch.randint(0, Pb.shape[0], (131072,), device="cuda", generator=gen)
+        Xs.append(Pb[idx].contiguous())
+        Ts.append(W[idx][:, perm].contiguous())
+        del y, y0, Pb, W
+    X, T = torch.cat(Xs), torch.cat(Ts)
+    del Xs, Ts
+    dims = ctx.mlp_dims(Nk, H1, H2, K, ldx=ldb, x_bf16=True, weights_bf16=True)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0[0].record(ctx.stream)
+    prm, hist = lw.train(ctx, dims, X, T, steps=3000, batch=4096, lr=2e-3, log_every=1000)
+    t0[1].record(ctx.stream)
+    torch.cuda.synchronize()
+    train_ms = t0[0].elapsed_time(t0[1])
+    del X, T
+    torch.cuda.empty_cache()
+
+    held = synth.make_problem(N=256, Nr=128, Nc=256, Nv=120, Nk=Nk, Nm=K, I0=50, seed=6000, spectra=lib,
+                              three_d=True)
+    g = held.geom
+    y, y0 = synth.counts_torch(held, device="cuda")
+    # objectives against the FP32 P
+    P32 = ctx.normalise(y, y0)
+    Dp, Wp, obj_p = ctx.decompose(P32, Nk, K, iters, init=fhr.INIT_NNDSVD)
+    f_plain = _objective(P32, Nk, Dp, Wp)
+    obj_p = obj_p.cpu().numpy()
+    n_plain_tol = _first_within(obj_p, obj_p[-1] * (1 + 1e-3))
+    del Wp
+    Pb = ctx.normalise(y, y0, p_dtype=fhr.BF16)
+    target = f_plain * (1 + 1e-3)
+
+    def reach(**kw):
+        """Fewest iterations on the BF16 P whose factors reach the target on the FP32 P."""
+        D_, W_, ob = ctx.decompose(Pb, Nk, K, iters, **kw)
+        ob = ob.cpu().numpy()
+        off = _objective(P32, Nk, D_, W_) - float(ob[-1])   # FP32-P minus BF16-P objective near the end
+        del W_
+        n_ = _first_within(ob + off, target) or iters
+        f_ = None
+        while n_ <= iters:
+            D_, W_, _ = ctx.decompose(Pb, Nk, K, n_, obj=False, **kw)
+            f_ = _objective(P32, Nk, D_, W_)
+            del W_
+            if f_ <= target:
+                break
+            n_ += 1
+        return min(n_, iters), f_
+
+    n, f_learn = reach(mlp=(dims, prm))
+    n_pb, f_pb = reach(init=fhr.INIT_NNDSVD)
+    reached = f_learn is not None and f_learn <= target
+    del P32, Pb
+    torch.cuda.empty_cache()
+
+    xh = torch.empty((g.Nr, g.N, g.N, Nk), dtype=torch.bfloat16, device="cuda")
+    Dout = torch.empty((Nk, K), dtype=torch.float32, device="cuda")
+
+    def run_pipeline(p_dtype, init, nmf_iters):
+        prm_p = ctx.pipeline_params(Nv=g.Nv, Nr=g.Nr, Nc=g.Nc, Nk=Nk, N=g.N, K=K, nmf_iters=nmf_iters,
+                                    mbir_iters=MBIR_ITERS, momentum=True, p_dtype=p_dtype, xh_dtype=fhr.BF16,
+                                    init=init)
+        if init == fhr.INIT_LEARNED:
+            prm_p.nmf.mlp = ctypes.addressof(dims)
+            prm_p.nmf.mlp_params = prm.data_ptr()
+        ws, wsb = ctx.pipeline_workspace(prm_p)
+        ob = torch.empty(max(nmf_iters, 1), dtype=torch.float64, device="cuda")
+        go = lambda: ctx.pipeline(prm_p, y, y0, Dout, xh, obj=ob, ws=ws, ws_bytes=wsb)
+        go()
+        ctx.check(ctx.status(ws))
+        ctx.profile(True)
+        ms = _timed(ctx, go)
+        fams = {k: round(ctx.profile_read(k)[1], 2) for k in ("normalise", "nndsvd_pass", "nmf_pass", "mlp_forward",
+                                                              "proj_fwd", "mbir_update", "expand")}
+        ctx.profile(False)
+        ctx.check(ctx.status(ws))
+        del ws
+        torch.cuda.empty_cache()
+        return ms, fams
+
+    t_plain, k_plain = run_pipeline(fhr.F32, fhr.INIT_NNDSVD, iters)
+    t_plain_tol, _ = run_pipeline(fhr.F32, fhr.INIT_NNDSVD, n_plain_tol)
+    t_lb, k_lb = run_pipeline(fhr.BF16, fhr.INIT_LEARNED, n)
+    t_pb, _ = run_pipeline(fhr.BF16, fhr.INIT_NNDSVD, n_pb)
+    vb = g.Nr * g.N * g.N * Nk
+    print(json.dumps({
+        "case": "learned", "workload": "256x256x128 volume, Nk=1500, 120 views, K=6, 50 counts/bin",
+        "train": {"phantoms": n_train, "rows": n_train * 131072, "steps": 3000, "batch": 4096, "ms": round(train_ms, 1),
+                  "loss": hist},
+        "plain_f32": {"iters": iters, "objective_fp32P": f_plain, "pipeline_ms": round(t_plain, 2),
+                      "voxel_bins_per_s": vb / (t_plain / 1e3), "kernel_ms": k_plain},
+        "plain_f32_own_tol": {"iters": n_plain_tol, "pipeline_ms": round(t_plain_tol, 2)},
+        "learned_bf16": {"iters": n, "objective_fp32P": f_learn, "reached_plain_within_1e-3": bool(reached),
+                         "rel_to_plain": (f_learn / f_plain - 1.0) if f_learn else None,
+                         "pipeline_ms": round(t_lb, 2), "voxel_bins_per_s": vb / (t_lb / 1e3), "kernel_ms": k_lb},
+        "plain_bf16_nndsvd": {"iters": n_pb, "objective_fp32P": f_pb,
+                              "reached_plain_within_1e-3": bool(f_pb is not None and f_pb <= target),
+                              "pipeline_ms": round(t_pb, 2)},
+        "speedup_vs_plain_f32": round(t_plain / t_lb, 3),
+        "speedup_vs_plain_f32_own_tol": round(t_plain_tol / t_lb, 3)}), flush=True)
+    ctx.close()
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "precision"
     if case == "precision":
         precision()
+    elif case == "learned":
+        learned(int(sys.argv[2]) if len(sys.argv) > 2 else 12)
     elif case == "batched":
         batched(int(sys.argv[2]) if len(sys.argv) > 2 else 40, int(sys.argv[3]) if len(sys.argv) > 3 else 100)
     else:

@@ -106,3 +106,38 @@ def test_host_io_back_to_back_calls(fx):
         refs.append(_run_gpu(fx, pb_, K, 20, 5)[3])
         np.testing.assert_array_equal(xh.numpy(), refs[-1])
     assert not np.array_equal(refs[0], refs[1])
+
+
+def test_learned_start_in_the_pipeline(fx):
+    # Algorithm 1 from the learned start on BF16 P: the decomposition inside the pipeline
+    # equals fhr_decompose from the same network on the same normalised P
+    import ctypes
+
+    import torch
+    from paper_2410_22500_gb300 import fhr, learned, synth
+
+    pb = synth.scaled(synth.tiny_2d, Nk=96, Nv=40)
+    g = pb.geom
+    K, iters = 3, 15
+    ldb = (pb.Nk + 7) // 8 * 8
+    dims = fx.mlp_dims(pb.Nk, 32, 16, K, ldx=ldb, x_bf16=True, weights_bf16=True)
+    params = torch.from_numpy(learned.init_params(np.random.default_rng(4), pb.Nk, 32, 16, K)).cuda()
+    y, y0 = synth.counts_numpy(pb)
+    yt, y0t = torch.from_numpy(y.view(np.int16)).cuda(), torch.from_numpy(y0.view(np.int16)).cuda()
+    prm = fx.pipeline_params(Nv=g.Nv, Nr=g.Nr, Nc=g.Nc, Nk=pb.Nk, N=g.N, K=K, nmf_iters=iters, mbir_iters=3,
+                             p_dtype=fhr.BF16, init=fhr.INIT_LEARNED)
+    prm.nmf.mlp = ctypes.addressof(dims)
+    prm.nmf.mlp_params = params.data_ptr()
+    D = torch.empty((pb.Nk, K), dtype=torch.float32, device="cuda")
+    obj = torch.empty(iters, dtype=torch.float64, device="cuda")
+    xh = torch.empty((g.Nr, g.N, g.N, pb.Nk), dtype=torch.float32, device="cuda")
+    ws = fx.pipeline(prm, yt, y0t, D, xh, obj=obj)
+    assert fx.status(ws) == 0
+    P = fx.normalise(yt, y0t, p_dtype=fhr.BF16)
+    D2, _, obj2 = fx.decompose(P, pb.Nk, K, iters, mlp=(dims, params))
+    np.testing.assert_array_equal(D.cpu().numpy(), D2.cpu().numpy())
+    np.testing.assert_array_equal(obj.cpu().numpy(), obj2.cpu().numpy())
+    assert np.isfinite(xh.cpu().numpy()).all()
+    prm.nmf.init = fhr.INIT_GIVEN
+    with pytest.raises(fhr.FhrError):
+        fx.pipeline_workspace(prm)
