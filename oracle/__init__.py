@@ -66,7 +66,7 @@ def lib():
             _lib = ctypes.CDLL(build())
             L = _lib
             L.or_normalise.restype = ctypes.c_int
-            L.or_normalise.argtypes = [ctypes.c_int] * 4 + [_u16p, _u16p, _u8p, _u8p, _dp, _dp]
+            L.or_normalise.argtypes = [ctypes.c_int] * 4 + [_u16p, _u16p, _u8p, _u8p, ctypes.c_int, _dp, _dp]
             L.or_hals_update_W.argtypes = [ctypes.c_long, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
             L.or_hals_update_D.argtypes = [ctypes.c_long, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
             L.or_normalise_columns.argtypes = [ctypes.c_long, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
@@ -115,7 +115,10 @@ def normalise(y, y0, bg=None, dead=None, return_offset=False):
     """Eq. (neglogattenuation) with the offset correction of Appendix A.
 
     y [Nv][Nr][Nc][Nk] uint16, y0 [Nr][Nc][Nk] uint16 -> P [Nv*Nc*Nr][Nk]
-    (pixel order (v, c, r)).  bg: [Nr][Nc] background mask, dead: [Nk] mask."""
+    (pixel order (v, c, r)).  bg: [Nr][Nc] background mask; dead: [Nk] mask of dead
+    bins or [Nr][Nc][Nk] mask of dead (detector pixel, bin) entries.  Dead entries give
+    p = 0 and are left out of the background mean (a (v, k) with no live background
+    entry gets b = 0)."""
     y = np.ascontiguousarray(y, dtype=np.uint16)
     y0 = np.ascontiguousarray(y0, dtype=np.uint16)
     Nv, Nr, Nc, Nk = y.shape
@@ -125,9 +128,13 @@ def normalise(y, y0, bg=None, dead=None, return_offset=False):
     bg_keep = None if bg is None else np.ascontiguousarray(bg, dtype=np.uint8)
     bgp = None if bg_keep is None else bg_keep.ctypes.data_as(_u8p)
     dead_keep = None if dead is None else np.ascontiguousarray(dead, dtype=np.uint8)
+    per_pixel = 0
+    if dead_keep is not None:
+        per_pixel = int(dead_keep.ndim == 3)
+        assert dead_keep.shape == ((Nr, Nc, Nk) if per_pixel else (Nk,))
     dp = None if dead_keep is None else dead_keep.ctypes.data_as(_u8p)
     rc = lib().or_normalise(Nv, Nr, Nc, Nk, y.ctypes.data_as(_u16p), y0.ctypes.data_as(_u16p),
-                            bgp, dp, _d(P), _d(b))
+                            bgp, dp, per_pixel, _d(P), _d(b))
     if rc:
         raise ValueError("or_normalise failed: %d" % rc)
     return (P, b) if return_offset else P

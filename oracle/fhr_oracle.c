@@ -47,31 +47,34 @@ static double dmin(double a, double b) { return a < b ? a : b; }
 int or_normalise(int Nv, int Nr, int Nc, int Nk,
                  const uint16_t *y, const uint16_t *y0,
                  const uint8_t *bg,   /* [Nr][Nc] or NULL */
-                 const uint8_t *dead, /* [Nk] or NULL */
+                 const uint8_t *dead, /* [Nk] (per_pixel = 0) or [Nr][Nc][Nk] (per_pixel = 1), or NULL */
+                 int per_pixel,
                  double *P,           /* [Nv*Nc*Nr][Nk] */
                  double *b_out)       /* [Nv][Nk] or NULL */
 {
     if (Nv <= 0 || Nr <= 0 || Nc <= 0 || Nk <= 0) return OR_ERR_ARG;
     double *b = (double *)calloc((size_t)Nv * Nk, sizeof(double));
     if (!b) return OR_ERR_NOMEM;
+    /* a dead entry (detector pixel (r, c), bin k) carries no measurement */
+#define OR_DEAD(r, c, k) \
+    (dead && (per_pixel ? dead[((size_t)(r) * Nc + (c)) * Nk + (k)] : dead[(k)]))
     if (bg) {
-        long nb = 0;
-        for (int r = 0; r < Nr; ++r)
-            for (int c = 0; c < Nc; ++c) nb += bg[r * Nc + c] ? 1 : 0;
-        if (nb > 0) {
-            for (int v = 0; v < Nv; ++v)
-                for (int k = 0; k < Nk; ++k) {
-                    double s = 0.0;
-                    for (int r = 0; r < Nr; ++r)
-                        for (int c = 0; c < Nc; ++c) {
-                            if (!bg[r * Nc + c]) continue;
-                            double yy = y[(((size_t)v * Nr + r) * Nc + c) * Nk + k];
-                            double yo = y0[((size_t)r * Nc + c) * Nk + k];
-                            s += log(dmax(yo, 1.0)) - log(dmax(yy, 1.0));
-                        }
-                    b[(size_t)v * Nk + k] = s / (double)nb;
-                }
-        }
+        /* Appendix A: b_{v,k} = mean of -log(y/y0) over the background pixels whose
+           entry is live; 0 when there is none */
+        for (int v = 0; v < Nv; ++v)
+            for (int k = 0; k < Nk; ++k) {
+                double s = 0.0;
+                long n = 0;
+                for (int r = 0; r < Nr; ++r)
+                    for (int c = 0; c < Nc; ++c) {
+                        if (!bg[r * Nc + c] || OR_DEAD(r, c, k)) continue;
+                        double yy = y[(((size_t)v * Nr + r) * Nc + c) * Nk + k];
+                        double yo = y0[((size_t)r * Nc + c) * Nk + k];
+                        s += log(dmax(yo, 1.0)) - log(dmax(yy, 1.0));
+                        ++n;
+                    }
+                b[(size_t)v * Nk + k] = n > 0 ? s / (double)n : 0.0;
+            }
     }
     for (int v = 0; v < Nv; ++v)
         for (int r = 0; r < Nr; ++r)
@@ -83,10 +86,11 @@ int or_normalise(int Nv, int Nr, int Nc, int Nk,
                     double p = log(dmax(yo, 1.0)) - log(dmax(yy, 1.0));
                     p -= b[(size_t)v * Nk + k];
                     p = dmax(p, 0.0);
-                    if (dead && dead[k]) p = 0.0;
+                    if (OR_DEAD(r, c, k)) p = 0.0;
                     P[j * Nk + k] = p;
                 }
             }
+#undef OR_DEAD
     if (b_out) memcpy(b_out, b, sizeof(double) * (size_t)Nv * Nk);
     free(b);
     return OR_OK;

@@ -107,3 +107,56 @@ def test_noise_free_projection_recovered(orc):
     pv = p.transpose(0, 2, 1, 3).reshape(-1, pb.Nk)  # (v, c, r) order
     bound = 0.6 / np.maximum(y.transpose(0, 2, 1, 3).reshape(-1, pb.Nk).astype(float), 1)
     assert np.all(np.abs(P - pv) <= bound + 1e-12)
+
+
+def test_dead_pixel_bins_zero_and_rest_unchanged(orc):
+    # a per-(detector pixel, bin) mask zeroes exactly those entries in every view
+    rng = np.random.default_rng(4)
+    Nv, Nr, Nc, Nk = 3, 2, 4, 9
+    y = rng.integers(0, 500, size=(Nv, Nr, Nc, Nk)).astype(np.uint16)
+    y0 = rng.integers(400, 900, size=(Nr, Nc, Nk)).astype(np.uint16)
+    dead = (rng.uniform(size=(Nr, Nc, Nk)) < 0.2).astype(np.uint8)
+    P = orc.normalise(y, y0, dead=dead)
+    P2 = orc.normalise(y, y0)
+    for v in range(Nv):
+        for r in range(Nr):
+            for c in range(Nc):
+                j = (v * Nc + c) * Nr + r
+                m = dead[r, c].astype(bool)
+                assert np.all(P[j, m] == 0)
+                np.testing.assert_array_equal(P[j, ~m], P2[j, ~m])
+
+
+def test_per_bin_mask_equals_its_broadcast(orc):
+    rng = np.random.default_rng(5)
+    Nv, Nr, Nc, Nk = 2, 3, 4, 7
+    y = rng.integers(0, 300, size=(Nv, Nr, Nc, Nk)).astype(np.uint16)
+    y0 = rng.integers(200, 600, size=(Nr, Nc, Nk)).astype(np.uint16)
+    bg = np.zeros((Nr, Nc), np.uint8)
+    bg[:, 0] = 1
+    dead = np.zeros(Nk, np.uint8)
+    dead[[2, 5]] = 1
+    Pa, ba = orc.normalise(y, y0, bg=bg, dead=dead, return_offset=True)
+    Pb, bb = orc.normalise(y, y0, bg=bg, dead=np.broadcast_to(dead, (Nr, Nc, Nk)).copy(), return_offset=True)
+    np.testing.assert_array_equal(Pa, Pb)
+    np.testing.assert_array_equal(ba, bb)
+    assert np.all(ba[:, [2, 5]] == 0)      # no live background entry
+
+
+def test_background_mean_skips_dead_entries(orc):
+    # App. A offset with two background pixels, one of them dead in bin 1 with zero counts:
+    # b is then the other pixel's -log(y/y0) alone (worked by hand: ln(800/200) = 2 ln 2),
+    # and the planted offset is removed from the object pixel
+    y0 = np.full((1, 3, 2), 800, np.uint16)
+    y = np.zeros((1, 1, 3, 2), np.uint16)
+    y[0, 0, 0] = [400, 200]                 # background pixel 0: b = ln 2, 2 ln 2
+    y[0, 0, 1] = [400, 0]                   # background pixel 1: bin 1 dead (no counts)
+    y[0, 0, 2] = [100, 50]                  # object pixel
+    bg = np.array([[1, 1, 0]], np.uint8)
+    dead = np.zeros((1, 3, 2), np.uint8)
+    dead[0, 1, 1] = 1
+    P, b = orc.normalise(y, y0, bg=bg, dead=dead, return_offset=True)
+    np.testing.assert_allclose(b[0], [math.log(2.0), 2 * math.log(2.0)], rtol=1e-15)
+    np.testing.assert_allclose(P[2], [math.log(8.0) - math.log(2.0), math.log(16.0) - 2 * math.log(2.0)],
+                               rtol=1e-15)
+    assert P[1, 1] == 0.0
