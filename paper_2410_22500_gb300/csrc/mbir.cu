@@ -88,9 +88,9 @@ __global__ void __launch_bounds__(1024) mbir_update_kernel(const float *__restri
                                                            const float *__restrict__ dA, const MbirChan *__restrict__ chp,
                                                            MbirPrior pr, float mom_a, int N, int Nc, int Nv, int Nr,
                                                            int K, int Wl, int Wc) {
-    const GatherIdx gi = gather_idx<VW * G>(N * N, Wl, Wc);
+    const GatherIdx gi = gather_idx<VW, G>(N * N, Wl, Wc);
     if (!gi.ok) return;
-    mbir_update_at<VW, G>(e, z, xprev, xnew, znext, t, dA, chp, pr, mom_a, N, Nc, Nv, Nr, K, Wl, gi.item, gi.w0);
+    mbir_update_at<VW, G>(e, z, xprev, xnew, znext, t, dA, chp, pr, mom_a, N, Nc, Nv, Nr, K, Wl, gi.item, gi.w0, gi.gs);
 }
 
 struct MbirWs {
@@ -143,7 +143,7 @@ static fhr_status launch_update_g(fhr_ctx *ctx, const fhr_geom *g, const GatherS
 
 static fhr_status launch_update(fhr_ctx *ctx, const fhr_geom *g, const MbirWs &w, const float *z, const float *xp,
                                 float *xn, float *zn, const MbirPrior &pr, float a, int K, int Wl) {
-    const GatherShape s = gather_shape(Wl, gather_slab_values(g));
+    const GatherShape s = gather_shape(Wl, gather_slab_values(g), kGatherMaxGBwd);
     if (s.vw == 4 && s.g == 2) return launch_update_g<4, 2>(ctx, g, s, w, z, xp, xn, zn, pr, a, K, Wl);
     if (s.vw == 4) return launch_update_g<4, 1>(ctx, g, s, w, z, xp, xn, zn, pr, a, K, Wl);
     return launch_update_g<1, 1>(ctx, g, s, w, z, xp, xn, zn, pr, a, K, Wl);

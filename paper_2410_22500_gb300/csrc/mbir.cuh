@@ -125,7 +125,7 @@ __device__ __forceinline__ void mbir_update_group(const typename VecF<VW>::T &bp
 }
 
 
-// SQS update of one pixel for the G groups of VW values starting at w0: one
+// SQS update of one pixel for the G groups of VW values at w0 + g gs: one
 // backward gather (shared table reads), then the update of each group.
 template <int VW, int G, bool COH = false>
 __device__ __forceinline__ void mbir_update_at(const float *__restrict__ e, const float *__restrict__ z,
@@ -133,13 +133,13 @@ __device__ __forceinline__ void mbir_update_at(const float *__restrict__ e, cons
                                                float *__restrict__ znext, const ProjTables &t,
                                                const float *__restrict__ dA, const MbirChan *__restrict__ chp,
                                                const MbirPrior &pr, float mom_a, int N, int Nc, int Nv, int Nr, int K,
-                                               int Wl, int pix, int w0) {
+                                               int Wl, int pix, int w0, int gs) {
     typename VecF<VW>::T bp[G];
-    backproject_at<VW, G, COH>(e, t, N, Nc, Nv, Wl, pix, w0, bp);
+    backproject_at<VW, G, COH>(e, t, N, Nc, Nv, Wl, pix, w0, gs, bp);
 #pragma unroll
     for (int g = 0; g < G; ++g)
         mbir_update_group<VW, COH>(bp[g], z, xprev, xnew, znext, dA, chp, pr, mom_a, N, Nc, Nv, Nr, K, Wl, pix,
-                                   w0 + g * VW);
+                                   w0 + g * gs);
 }
 
 }  // namespace fhr

@@ -90,7 +90,7 @@ __device__ __forceinline__ void batch_forward(const BatchItem &item, const Batch
     for (int r = tid / CH; r < item.count; r += sweep) {
         const int row = item.start + r;
         typename VF::T axs[1];
-        forward_at<VW, 1, true>(z, P.t, P.N, P.Nc, P.Wl, row, ch * VW, axs);
+        forward_at<VW, 1, true>(z, P.t, P.N, P.Nc, P.Wl, row, ch * VW, VW, axs);
         typename VF::T ax = axs[0];
         const size_t o = (size_t)row * P.Wl + ch * VW;
         const typename VF::T v = VF::ld(P.sino + o);
@@ -109,7 +109,7 @@ __device__ __forceinline__ void batch_update(const BatchItem &item, const BatchP
     if (tid >= sweep * CH) return;
     for (int r = tid / CH; r < item.count; r += sweep)
         mbir_update_at<VW, 1, true>(P.e, z, xprev, xnew, znext, P.t, P.dA, P.chan, pr, mom, P.N, P.Nc, P.Nv, P.Nr, P.K,
-                                 P.Wl, item.start + r, ch * VW);
+                                    P.Wl, item.start + r, ch * VW, VW);
 }
 
 // Next work item of a phase: items are taken in list order (largest first)
@@ -122,7 +122,7 @@ __device__ __forceinline__ int next_item(unsigned *ctr) {
     return idx;
 }
 
-__global__ void __launch_bounds__(kBatchThreads) mbir_batch_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, 65536 / (kBatchThreads * 64)) mbir_batch_kernel(BatchArgs a) {
     for (int it = 0; it < a.iters; ++it) {
         const int par = it & 1;
         // ---- phase F: residual e = V - A z

@@ -125,6 +125,7 @@ fhr_status proj_build_tables(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &
 
 template <template <int, int> class Launch, typename... A>
 static fhr_status gather_dispatch(const GatherShape &s, A... args) {
+    if (s.vw == 4 && s.g == 4) return Launch<4, 4>::run(s, args...);
     if (s.vw == 4 && s.g == 2) return Launch<4, 2>::run(s, args...);
     if (s.vw == 4) return Launch<4, 1>::run(s, args...);
     return Launch<1, 1>::run(s, args...);
@@ -152,12 +153,12 @@ struct BwdLaunch {
 
 fhr_status proj_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *x, float *y,
                         const float *V) {
-    const GatherShape s = gather_shape(Wl, gather_slab_values(g));
+    const GatherShape s = gather_shape(Wl, gather_slab_values(g), kGatherMaxGFwd);
     return gather_dispatch<FwdLaunch>(s, ctx, g, t, Wl, x, y, V);
 }
 
 fhr_status proj_backward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *y, float *x) {
-    const GatherShape s = gather_shape(Wl, gather_slab_values(g));
+    const GatherShape s = gather_shape(Wl, gather_slab_values(g), kGatherMaxGBwd);
     return gather_dispatch<BwdLaunch>(s, ctx, g, t, Wl, y, x);
 }
 

@@ -80,10 +80,10 @@ __device__ __forceinline__ typename VecF<VW>::T ldv(const float *p) {
 }
 
 // sum over lines and candidates of A * x[pixel][w] for one ray (item = (v, c)),
-// the G groups of VW values starting at w0 (one table read serves all groups).
+// the G groups of VW values at w0 + g gs (one table read serves all groups).
 template <int VW, int G, bool COH = false>
 __device__ __forceinline__ void forward_at(const float *__restrict__ x, const ProjTables &t, int N, int Nc, int Wl,
-                                           int item, int w0, typename VecF<VW>::T (&acc)[G]) {
+                                           int item, int w0, int gs, typename VecF<VW>::T (&acc)[G]) {
     using VF = VecF<VW>;
     const int v = item / Nc, c = item - v * Nc;
     const bool rows = t.rowmaj[v] != 0;
@@ -101,19 +101,19 @@ __device__ __forceinline__ void forward_at(const float *__restrict__ x, const Pr
         const size_t qs = (size_t)qstride * Wl;
         if (w.x != 0.f) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.x, ldv<VW, COH>(xp + g * VW));
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.x, ldv<VW, COH>(xp + g * gs));
         }
         if (w.y != 0.f) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.y, ldv<VW, COH>(xp + qs + g * VW));
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.y, ldv<VW, COH>(xp + qs + g * gs));
         }
         if (w.z != 0.f) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.z, ldv<VW, COH>(xp + 2 * qs + g * VW));
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.z, ldv<VW, COH>(xp + 2 * qs + g * gs));
         }
         if (w.w != 0.f) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.w, ldv<VW, COH>(xp + 3 * qs + g * VW));
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.w, ldv<VW, COH>(xp + 3 * qs + g * gs));
         }
     }
 }
@@ -121,21 +121,25 @@ __device__ __forceinline__ void forward_at(const float *__restrict__ x, const Pr
 // Gathers over a vector of Wl values per pixel / ray run in channel chunks of
 // Wc values (Wc | Wl, VW | Wc), chunk-major over the grid: the blocks resident
 // at one time touch one chunk of the image / sinogram, which stays in L2 when
-// the whole does not.  Thread = (item, VWG = VW * G consecutive values of the chunk).
+// the whole does not.  Thread = (item, G groups of VW values); the CH = Wc /
+// (VW G) threads of an item take VW values each per group, so that group g of
+// the item is the contiguous run w0 + g gs (gs = CH VW) across those threads
+// and every load instruction of a warp reads whole sectors once.
 struct GatherIdx {
-    int item, w0;
+    int item, w0, gs;
     bool ok;
 };
 
-template <int VWG>
+template <int VW, int G>
 __device__ __forceinline__ GatherIdx gather_idx(int items, int Wl, int Wc) {
-    const int CH = Wc / VWG;
+    const int CH = Wc / (VW * G);
     const int ipb = blockDim.x / CH;
     const int bpc = (items + ipb - 1) / ipb;   // blocks per chunk
     const int chunk = blockIdx.x / bpc;
     GatherIdx r;
     r.item = (blockIdx.x - chunk * bpc) * ipb + threadIdx.x / CH;
-    r.w0 = chunk * Wc + (threadIdx.x % CH) * VWG;
+    r.w0 = chunk * Wc + (threadIdx.x % CH) * VW;
+    r.gs = CH * VW;
     r.ok = threadIdx.x < ipb * CH && r.item < items && r.w0 < Wl;
     return r;
 }
@@ -147,28 +151,29 @@ __global__ void __launch_bounds__(1024) proj_fwd_kernel(const float *__restrict_
                                                         const float *__restrict__ V, ProjTables t, int N, int Nc,
                                                         int Nv, int Wl, int Wc) {
     using VF = VecF<VW>;
-    const GatherIdx gi = gather_idx<VW * G>(Nv * Nc, Wl, Wc);
+    const GatherIdx gi = gather_idx<VW, G>(Nv * Nc, Wl, Wc);
     if (!gi.ok) return;
     const int item = gi.item;
     typename VF::T acc[G];
-    forward_at<VW, G>(x, t, N, Nc, Wl, item, gi.w0, acc);
+    forward_at<VW, G>(x, t, N, Nc, Wl, item, gi.w0, gi.gs, acc);
     float *yo = y + (size_t)item * Wl + gi.w0;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         if (V) {
-            typename VF::T vv = VF::ld(V + (size_t)item * Wl + gi.w0 + g * VW);
+            typename VF::T vv = VF::ld(V + (size_t)item * Wl + gi.w0 + g * gi.gs);
 #pragma unroll
             for (int e = 0; e < VW; ++e) VF::set(acc[g], e, VF::get(vv, e) - VF::get(acc[g], e));
         }
-        VF::st(yo + g * VW, acc[g]);
+        VF::st(yo + g * gi.gs, acc[g]);
     }
 }
 
 // x[pixel][w] = sum over views and candidate bins of A * y[v][c][w], for the
-// G groups of VW values starting at w0.
+// G groups of VW values at w0 + g gs.
 template <int VW, int G, bool COH = false>
 __device__ __forceinline__ void backproject_at(const float *__restrict__ y, const ProjTables &t, int N, int Nc,
-                                               int Nv, int Wl, int pix, int w0, typename VecF<VW>::T (&acc)[G]) {
+                                               int Nv, int Wl, int pix, int w0, int gs,
+                                               typename VecF<VW>::T (&acc)[G]) {
     using VF = VecF<VW>;
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = VF::zero();
@@ -179,15 +184,15 @@ __device__ __forceinline__ void backproject_at(const float *__restrict__ y, cons
         const float *yr = yc + ((size_t)v * Nc + (int)w.w) * Wl;
         if (w.x != 0.f) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.x, ldv<VW, COH>(yr + g * VW));
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.x, ldv<VW, COH>(yr + g * gs));
         }
         if (w.y != 0.f) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.y, ldv<VW, COH>(yr + Wl + g * VW));
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.y, ldv<VW, COH>(yr + Wl + g * gs));
         }
         if (w.z != 0.f) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.z, ldv<VW, COH>(yr + 2 * (size_t)Wl + g * VW));
+            for (int g = 0; g < G; ++g) VF::fma(acc[g], w.z, ldv<VW, COH>(yr + 2 * (size_t)Wl + g * gs));
         }
     }
 }
@@ -196,12 +201,12 @@ template <int VW, int G>
 __global__ void __launch_bounds__(1024) proj_bwd_kernel(const float *__restrict__ y, float *__restrict__ x,
                                                         ProjTables t, int N, int Nc, int Nv, int Wl, int Wc) {
     using VF = VecF<VW>;
-    const GatherIdx gi = gather_idx<VW * G>(N * N, Wl, Wc);
+    const GatherIdx gi = gather_idx<VW, G>(N * N, Wl, Wc);
     if (!gi.ok) return;
     typename VF::T acc[G];
-    backproject_at<VW, G>(y, t, N, Nc, Nv, Wl, gi.item, gi.w0, acc);
+    backproject_at<VW, G>(y, t, N, Nc, Nv, Wl, gi.item, gi.w0, gi.gs, acc);
 #pragma unroll
-    for (int g = 0; g < G; ++g) VF::st(x + (size_t)gi.item * Wl + gi.w0 + g * VW, acc[g]);
+    for (int g = 0; g < G; ++g) VF::st(x + (size_t)gi.item * Wl + gi.w0 + g * gi.gs, acc[g]);
 }
 
 // Launch shape for the gathers: chunks of Wc values (the whole vector unless
@@ -209,6 +214,9 @@ __global__ void __launch_bounds__(1024) proj_bwd_kernel(const float *__restrict_
 // Wc / (VW G) threads per item, items per block so that a block holds about
 // `target` threads, and the grid = chunks x blocks per chunk.
 constexpr size_t kGatherSlab = (size_t)32 << 20;
+// groups per thread: the forward gather gains up to 4 (0.341 -> 0.287 ms on the
+// 128^2 x 64 slice / K = 5 shape), the fused backward + update is best at 2
+constexpr int kGatherMaxGFwd = 4, kGatherMaxGBwd = 2;
 
 struct GatherShape {
     int vw, g, wc, ch, ipb, threads;   // g: groups of vw values per thread
@@ -218,16 +226,19 @@ struct GatherShape {
     }
 };
 
-static inline GatherShape gather_shape(int Wl, size_t slab_values = 0, int target = 256) {
+static inline GatherShape gather_shape(int Wl, size_t slab_values, int max_g, int target = 256) {
     GatherShape g;
     g.vw = (Wl % 4 == 0) ? 4 : 1;
     g.wc = Wl;
     // halve the chunk while the slab of one chunk exceeds the L2 budget (keeping VW | Wc | Wl)
     while (slab_values * (size_t)g.wc * sizeof(float) > kGatherSlab && g.wc % (2 * g.vw) == 0 && g.wc / 2 >= 32)
         g.wc /= 2;
-    // two groups per thread (8 values) share each table read where the chunk allows it;
-    // four (60-64 registers) measured slower on the 128^2 x 64 / K=5 shape
-    g.g = (g.vw == 4 && g.wc % 8 == 0) ? 2 : 1;
+    // up to max_g groups per thread share each table read where the chunk allows it
+    g.g = 1;
+    if (g.vw == 4) {
+        if (max_g >= 4 && g.wc % 16 == 0) g.g = 4;
+        else if (max_g >= 2 && g.wc % 8 == 0) g.g = 2;
+    }
     g.ch = g.wc / (g.vw * g.g);
     g.ipb = std::max(1, target / g.ch);
     g.threads = g.ipb * g.ch;
