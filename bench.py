@@ -296,6 +296,7 @@ def run_ours(args, rank, world, device):
                      "peak": peak, "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
                      if peak_kind == "measured" else "fallback", "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "frac_of_nominal_7900": (achieved / 7900.0) if achieved else None,
                      "algorithmic_bytes_per_launch": pass_bytes, "launches": pass_n,
                      "avg_launch_ms": pass_ms / pass_n if pass_n else None},
         "kernel_ms": {n: {"launches": c, "total_ms": t} for n, (c, t) in fams.items()},

@@ -93,18 +93,21 @@ fhr_status fhr_workspace_status(fhr_ctx *ctx, void *ws);
  * offset correction of Appendix A, Eq. (back_offset): when bg_mask is given,
  * b_{v,k} = mean over background pixels of -log(y/y0) and p <- p - b.
  * Readings of points the paper leaves open: counts are clamped at 1 before
- * the logarithm; p is clamped at 0 afterwards (NMF needs p >= 0); bins with
- * dead_bins[k] != 0 give p = 0.
+ * the logarithm; p is clamped at 0 afterwards (NMF needs p >= 0); dead
+ * entries give p = 0 and are left out of the background mean (a (v, k) with
+ * no live background entry gets b = 0).
  *   y, y0      counts (layouts above)
  *   bg_mask    [Nr][Nc] uint8 or NULL; b_out [Nv][Nk] float receives b and
  *              is required when bg_mask is given (else may be NULL)
- *   dead_bins  [Nk] uint8 or NULL
+ *   dead_bins  uint8 or NULL: [Nk] (dead bins) or, with dead_per_pixel = 1,
+ *              [Nr][Nc][Nk] (dead detector pixel-bins, the same in every view)
  *   P          output [Np][ldP], FHR_F32 (ldP % 4 == 0) or FHR_BF16 (ldP % 8 == 0)
  * ---------------------------------------------------------------------- */
 typedef struct {
     int Nv, Nr, Nc, Nk;
-    int ldP;       /* >= Nk */
-    int p_dtype;   /* FHR_F32 or FHR_BF16 */
+    int ldP;              /* >= Nk */
+    int p_dtype;          /* FHR_F32 or FHR_BF16 */
+    int dead_per_pixel;   /* 0: dead_bins is [Nk]; 1: dead_bins is [Nr][Nc][Nk] */
 } fhr_norm_params;
 
 fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *prm,

@@ -187,37 +187,42 @@ __global__ void nmf_update_d(const double *Q64, const double *GW64, const double
         tot[tid] = a;
     }
     __syncthreads();
-    if (tid == 0) {
-        double dd[kMaxK], dtd[kMaxK * kMaxK];
-        for (int s = 0; s < K; ++s) dd[s] = tot[s];
-        const double dq = tot[K];
-        int o = K + 1;
-        for (int s = 0; s < K; ++s)
-            for (int t = s; t < K; ++t) {
-                dtd[s * K + t] = tot[o];
-                dtd[t * K + s] = tot[o];
-                ++o;
-            }
-        double f = *ssq64 - 2.0 * dq;
-        for (int i = 0; i < K * K; ++i) f += dtd[i] * gw[i];
-        *obj = f;
-        if (!isfinite(f)) report(status, FHR_ERR_NONFINITE);
-        double invn[kMaxK];
-        for (int s = 0; s < kMaxK; ++s) {
-            const double n = s < K ? sqrt(dd[s]) : 0.0;
-            invn[s] = n > 0.0 ? 1.0 / n : 1.0;
-            st_out->invn[s] = invn[s];
-            st_out->wscale[s] = n > 0.0 ? (float)n : 1.f;
-        }
-        for (int s = 0; s < kMaxK; ++s)
-            for (int t = 0; t < kMaxK; ++t)
-                st_out->G[s * kMaxK + t] = (s < K && t < K) ? (float)(dtd[s * K + t] * invn[s] * invn[t]) : 0.f;
-        for (int s = 0; s < kMaxK; ++s) {
-            const double gd = s < K ? dtd[s * K + s] * invn[s] * invn[s] : 0.0;
+    // The state from the totals, one thread per entry (an FP64 warp instruction
+    // costs about the same with one active lane as with 32, so no serial chains).
+    __shared__ double sdtd[kMaxK * kMaxK], sinvn[kMaxK];
+    if (tid < K * K) {   // D^T D from the packed upper triangle
+        const int s = tid / K, t = tid % K;
+        const int lo = s < t ? s : t, hi = s < t ? t : s;
+        sdtd[tid] = tot[K + 1 + lo * K - lo * (lo - 1) / 2 + (hi - lo)];
+    }
+    if (tid < kMaxK) {   // column norms: D is normalised, V scaled by the norms
+        const double n = tid < K ? sqrt(tot[tid]) : 0.0;
+        const double in = n > 0.0 ? 1.0 / n : 1.0;
+        sinvn[tid] = in;
+        st_out->invn[tid] = in;
+        st_out->wscale[tid] = n > 0.0 ? (float)n : 1.f;
+    }
+    __syncthreads();
+    if (tid < kMaxK * kMaxK) {   // Gram of the normalised D for the next pass
+        const int s = tid / kMaxK, t = tid % kMaxK;
+        const double gd = (s < K && t < K) ? sdtd[s * K + t] * sinvn[s] * sinvn[t] : 0.0;
+        st_out->G[tid] = (float)gd;
+        if (s == t) {
             st_out->Gdiag[s] = (float)gd;
             st_out->invdiag[s] = gd != 0.0 ? (float)(1.0 / gd) : 0.f;
         }
-        *counter = 0u;
+    }
+    if (tid < 32) {   // objective ||P||^2 - 2 <D, Q> + <D^T D, G_W>, fixed-order tree
+        double v = 0.0;
+        for (int i = tid; i < K * K; i += 32) v += sdtd[i] * gw[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (tid == 0) {
+            const double f = *ssq64 - 2.0 * tot[K] + v;
+            *obj = f;
+            if (!isfinite(f)) report(status, FHR_ERR_NONFINITE);
+            *counter = 0u;
+        }
     }
 }
 

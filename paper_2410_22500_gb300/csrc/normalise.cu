@@ -11,9 +11,15 @@ __device__ __forceinline__ float neglog_ratio(float y, float y0) {
     return logf(__fdiv_rn(fmaxf(y0, 1.f), fmaxf(y, 1.f)));
 }
 
-// b[v][k] = mean over background pixels (r, c) of -log(y/y0); compensated sum.
-__global__ void offset_reduce_kernel(const uint16_t *y, const uint16_t *y0, const uint8_t *bg, int Nv, int Nr,
-                                     int Nc, int Nk, float *b) {
+// dead entry (detector pixel (r, c), bin k): [Nk] or [Nr][Nc][Nk] mask
+__device__ __forceinline__ bool is_dead(const uint8_t *dead, int per_pixel, int r, int c, int Nc, int Nk, int k) {
+    return dead && (per_pixel ? dead[((size_t)r * Nc + c) * Nk + k] : dead[k]);
+}
+
+// b[v][k] = mean over the live background entries (r, c) of -log(y/y0)
+// (0 when there is none); compensated sum.
+__global__ void offset_reduce_kernel(const uint16_t *y, const uint16_t *y0, const uint8_t *bg, const uint8_t *dead,
+                                     int per_pixel, int Nv, int Nr, int Nc, int Nk, float *b) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y;
     if (k >= Nk) return;
@@ -21,7 +27,7 @@ __global__ void offset_reduce_kernel(const uint16_t *y, const uint16_t *y0, cons
     int nb = 0;
     for (int r = 0; r < Nr; ++r)
         for (int c = 0; c < Nc; ++c) {
-            if (!bg[r * Nc + c]) continue;
+            if (!bg[r * Nc + c] || is_dead(dead, per_pixel, r, c, Nc, Nk, k)) continue;
             ++nb;
             const float yy = y[(((size_t)v * Nr + r) * Nc + c) * Nk + k];
             const float yo = y0[((size_t)r * Nc + c) * Nk + k];
@@ -61,8 +67,9 @@ __device__ __forceinline__ void store1<__nv_bfloat16>(__nv_bfloat16 *dst, float 
 // VEC: counts rows are 16-byte aligned (Nk % 8 == 0), 8 counts per 16-byte load.
 template <bool VEC, typename TO>
 __global__ void __launch_bounds__(256) normalise_kernel(const uint16_t *__restrict__ y, const uint16_t *__restrict__ y0,
-                                                        const uint8_t *__restrict__ dead, const float *__restrict__ b,
-                                                        int Nv, int Nr, int Nc, int Nk, int ldP, TO *__restrict__ P) {
+                                                        const uint8_t *__restrict__ dead, int per_pixel,
+                                                        const float *__restrict__ b, int Nv, int Nr, int Nc, int Nk,
+                                                        int ldP, TO *__restrict__ P) {
     const int nch = (ldP + 7) / 8;
     const int64_t total = (int64_t)Nv * Nc * Nr * nch;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -99,7 +106,7 @@ __global__ void __launch_bounds__(256) normalise_kernel(const uint16_t *__restri
             float q = p[i];
             if (b && k < Nk) q -= b[(size_t)v * Nk + k];
             q = fmaxf(q, 0.f);
-            if (k >= Nk || (dead && dead[k])) q = 0.f;
+            if (k >= Nk || is_dead(dead, per_pixel, r, c, Nc, Nk, k)) q = 0.f;
             p[i] = q;
         }
         TO *dst = P + (size_t)j * ldP + k0;
@@ -120,6 +127,7 @@ extern "C" fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *p, cons
     FHR_ARG(p->Nv > 0 && p->Nr > 0 && p->Nc > 0 && p->Nk > 0, "sizes must be positive");
     FHR_ARG(p->ldP >= p->Nk, "ldP < Nk");
     FHR_ARG(p->p_dtype == FHR_F32 || p->p_dtype == FHR_BF16, "bad p_dtype");
+    FHR_ARG(p->dead_per_pixel == 0 || p->dead_per_pixel == 1, "dead_per_pixel must be 0 or 1");
     FHR_ARG(p->ldP % (p->p_dtype == FHR_BF16 ? 8 : 4) == 0, "ldP must make rows 16-byte aligned");
     FHR_ARG(y && y0 && P, "null pointer argument");
     FHR_ARG(!bg || b_out, "b_out is required with a background mask");
@@ -129,7 +137,8 @@ extern "C" fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *p, cons
     const float *b = nullptr;
     if (bg) {
         dim3 grid((unsigned)cdiv(p->Nk, 128), (unsigned)p->Nv);
-        offset_reduce_kernel<<<grid, 128, 0, st>>>(y, y0, bg, p->Nv, p->Nr, p->Nc, p->Nk, b_out);
+        offset_reduce_kernel<<<grid, 128, 0, st>>>(y, y0, bg, dead, p->dead_per_pixel, p->Nv, p->Nr, p->Nc, p->Nk,
+                                                   b_out);
         FHR_LAUNCHED();
         b = b_out;
     }
@@ -140,8 +149,9 @@ extern "C" fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *p, cons
     const int blocks = (int)std::min<int64_t>(cdiv(total, 256), (int64_t)ctx->sm_count * 16);
     const int ldp8 = p->ldP;
 #define LAUNCH(V, T)                                                                                     \
-    FHR_TIMED(TM_NORMALISE, (normalise_kernel<V, T><<<blocks, 256, 0, st>>>(y, y0, dead, b, p->Nv, p->Nr, p->Nc, \
-                                                                            p->Nk, ldp8, reinterpret_cast<T *>(P))))
+    FHR_TIMED(TM_NORMALISE, (normalise_kernel<V, T><<<blocks, 256, 0, st>>>(y, y0, dead, p->dead_per_pixel, b, p->Nv, \
+                                                                            p->Nr, p->Nc, p->Nk, ldp8,                \
+                                                                            reinterpret_cast<T *>(P))))
     if (p->p_dtype == FHR_F32) {
         if (vec) LAUNCH(true, float);
         else LAUNCH(false, float);

@@ -32,7 +32,7 @@ ENTRY_POINTS = (
 
 class NormParams(ctypes.Structure):
     _fields_ = [("Nv", ctypes.c_int), ("Nr", ctypes.c_int), ("Nc", ctypes.c_int), ("Nk", ctypes.c_int),
-                ("ldP", ctypes.c_int), ("p_dtype", ctypes.c_int)]
+                ("ldP", ctypes.c_int), ("p_dtype", ctypes.c_int), ("dead_per_pixel", ctypes.c_int)]
 
 
 class NmfParams(ctypes.Structure):
@@ -207,7 +207,8 @@ class Context:
 
     # ------------------------------------------------------------ normalise
     def normalise(self, y, y0, *, ldP=None, p_dtype=F32, bg=None, dead=None, P=None, b=None):
-        """Eq. (neglogattenuation) + Appendix A offset: counts -> P [Np][ldP]."""
+        """Eq. (neglogattenuation) + Appendix A offset: counts -> P [Np][ldP].  dead: [Nk] dead
+        bins or [Nr][Nc][Nk] dead detector pixel-bins (uint8)."""
         torch = _torch()
         Nv, Nr, Nc, Nk = y.shape
         mult = 8 if p_dtype == BF16 else 4
@@ -217,7 +218,7 @@ class Context:
                             device=y.device)
         if bg is not None and b is None:
             b = torch.empty((Nv, Nk), dtype=torch.float32, device=y.device)
-        prm = NormParams(Nv, Nr, Nc, Nk, ldP, p_dtype)
+        prm = NormParams(Nv, Nr, Nc, Nk, ldP, p_dtype, int(dead is not None and dead.dim() == 3))
         self.check(self.L.fhr_normalise(self._h, ctypes.byref(prm), _ptr(y), _ptr(y0), _ptr(bg), _ptr(dead),
                                         _ptr(b), _ptr(P)))
         return (P, b) if bg is not None else P
@@ -466,11 +467,11 @@ class Context:
     # ------------------------------------------------------------ pipeline
     def pipeline_params(self, *, Nv, Nr, Nc, Nk, N, K, nmf_iters, mbir_iters, p_dtype=F32, xh_dtype=F32,
                         host_io=False, power_iters=0, seed=0, angles=None, init=INIT_NNDSVD, kmeans_samples=0,
-                        kmeans_iters=0, recon=RECON_MBIR, **mbir_kw):
+                        kmeans_iters=0, recon=RECON_MBIR, dead_per_pixel=False, **mbir_kw):
         mult = 8 if p_dtype == BF16 else 4
         ldP = (Nk + mult - 1) // mult * mult
         prm = PipelineParams()
-        prm.norm = NormParams(Nv, Nr, Nc, Nk, ldP, p_dtype)
+        prm.norm = NormParams(Nv, Nr, Nc, Nk, ldP, p_dtype, int(dead_per_pixel))
         prm.nmf = NmfParams(Nv * Nr * Nc, Nk, ldP, K, nmf_iters, init, p_dtype, power_iters, seed, None, None,
                             kmeans_samples, kmeans_iters)
         prm.geom = self.geom(N, Nr, Nc, Nv, angles)

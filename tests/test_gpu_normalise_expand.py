@@ -54,6 +54,38 @@ def test_normalise_dead_bins_and_offset(fx, orc):
     assert float(P[:, [0, 5, 23]].abs().max()) == 0.0
 
 
+@pytest.mark.parametrize("p_dtype", ["f32", "bf16"])
+def test_normalise_dead_pixel_bins_and_offset(fx, orc, p_dtype):
+    # a per-(detector pixel, bin) mask, also inside the background region (those entries
+    # carry zero counts and must not enter the offset), a ragged Nk and a padded row
+    from paper_2410_22500_gb300 import fhr
+
+    rng = np.random.default_rng(102)
+    Nv, Nr, Nc, Nk = 6, 3, 11, 37
+    y0 = rng.integers(800, 1200, size=(Nr, Nc, Nk)).astype(np.uint16)
+    y = (y0[None] * rng.uniform(0.2, 1.1, size=(Nv, Nr, Nc, Nk))).astype(np.uint16)
+    bg = np.zeros((Nr, Nc), np.uint8)
+    bg[:, :3] = 1
+    dead = (rng.uniform(size=(Nr, Nc, Nk)) < 0.15).astype(np.uint8)
+    dead[:, :3, 4] = 1                     # bin 4 dead across the whole background
+    y[:, dead.astype(bool)] = 0
+    y0[dead.astype(bool)] = 0
+    pd = fhr.BF16 if p_dtype == "bf16" else fhr.F32
+    P, b = fx.normalise(_dev(y), _dev(y0), bg=_dev(bg), dead=_dev(dead), p_dtype=pd)
+    ref, bref = orc.normalise(y, y0, bg=bg, dead=dead, return_offset=True)
+    np.testing.assert_allclose(b.cpu().numpy(), bref, atol=5e-7, rtol=1e-6)
+    assert np.all(b.cpu().numpy()[:, 4] == 0)
+    got = P.float().cpu().numpy()[:, :Nk]
+    if p_dtype == "bf16":
+        np.testing.assert_allclose(got, ref, atol=2e-6, rtol=2 ** -8)
+    else:
+        np.testing.assert_allclose(got, ref, atol=2e-6, rtol=1e-6)
+    for v in range(Nv):
+        for r in range(Nr):
+            j = (v * Nc + np.arange(Nc)) * Nr + r
+            assert np.all(got[j][dead[r].astype(bool)] == 0)
+
+
 def test_normalise_bf16_rounding(fx, orc):
     import torch
     from paper_2410_22500_gb300 import fhr
