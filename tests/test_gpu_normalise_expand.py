@@ -149,3 +149,24 @@ def test_expand_bf16(fx, orc):
     xh = fx.expand(_dev(xs), _dev(D), N, Nr, xh_dtype=fhr.BF16).float().cpu().numpy()
     ref = orc.expand(xs.astype(np.float64), D.astype(np.float64), N, Nr)
     assert np.all(np.abs(xh - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-6)
+
+
+def test_expand_full_size_sampled(fx, orc):
+    # x^h for the 3-D workload (64 x 128 x 128 voxels x 1200 bins, 5 GB in f32), sampled pixels
+    # (every slice and bin of each) against the oracle's expansion of that pixel
+    import torch
+
+    N, Nr, K, Nk = 128, 64, 5, 1200
+    rng = np.random.default_rng(111)
+    xs = rng.uniform(0, 1, size=(N, N, Nr * K)).astype(np.float32)
+    D = rng.uniform(0, 1, size=(Nk, K)).astype(np.float32)
+    xh = fx.expand(_dev(xs), _dev(D), N, Nr)
+    pix = rng.choice(N * N, 48, replace=False)
+    pix[:2] = [0, N * N - 1]
+    for p in pix:
+        i, j = divmod(int(p), N)
+        got = xh[:, i, j, :].cpu().numpy()
+        ref = orc.expand(xs[i:i + 1, j:j + 1].astype(np.float64), D.astype(np.float64), 1, Nr)[:, 0, 0, :]
+        np.testing.assert_allclose(got, ref, rtol=K * 1.2e-7 * 4, atol=1e-7)
+    del xh
+    torch.cuda.empty_cache()

@@ -155,3 +155,24 @@ def test_mbir_channel_chunked_matches_oracle(fx, orc):
     ref = orc.mbir(V.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, iters=3, momentum=True)
     got = fx.reconstruct(_dev(V), N, Nr, K, 3, momentum=True).cpu().numpy()
     assert _rel(got, ref) <= 1e-4
+
+
+def test_full_size_projector_pair_and_mbir(fx, orc):
+    # the 3-D workload's shape in the benchmark's launch configuration (N = 128, 64 slices x
+    # K = 5 channels = 320 values per pixel, 90 views x 128 bins): both gathers and two MBIR
+    # iterations with momentum against the FP64 oracle over every output
+    N, Nc, Nv, Nr, K = 128, 128, 90, 64, 5
+    Wl = Nr * K
+    rng = np.random.default_rng(700)
+    x = rng.uniform(0, 1, size=(N, N, Wl)).astype(np.float32)
+    y = fx.project(_dev(x), Nc, Nv).cpu().numpy()
+    ref = orc.project(x.astype(np.float64), Nc, _angles(Nv))
+    assert _rel(y, ref) <= 1e-5
+    e = rng.normal(size=(Nv, Nc, Wl)).astype(np.float32)
+    xb = fx.backproject(_dev(e), N).cpu().numpy()
+    assert _rel(xb, orc.backproject(e.astype(np.float64), N, _angles(Nv))) <= 1e-5
+    V = ref.astype(np.float32)
+    sv, sx = orc.mbir_sigmas(V.astype(np.float64).reshape(-1, K), K, Nc)
+    got = fx.reconstruct(_dev(V), N, Nr, K, 2, momentum=True).cpu().numpy()
+    want = orc.mbir(V.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, iters=2, momentum=True)
+    assert _rel(got, want) <= 1e-4
