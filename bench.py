@@ -105,6 +105,24 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The slowest replica's value (a time): all-reduce MAX across the process group,
+    or x itself outside one."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, units_per_rank: float, ms: float) -> float:
+    """Units of all replicas per second over the max-over-ranks time (weak scaling)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def make_inputs(device):
     from paper_2410_22500_gb300 import synth
 
@@ -209,13 +227,10 @@ def run_ours(args, rank, world, device):
     clk = clocks.stop()
     if ctx.status(ws) != 0:
         raise RuntimeError("device status after timed steps")
-    if dist is not None:
-        t = torch.tensor([ms], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device)
     ms_step = ms / args.steps
     vb = g.Nr * g.N * g.N * pb.Nk
-    value = world * vb / (ms_step / 1e3)
+    value = whole_job_value(world, vb, ms_step)
 
     # ---- end to end through the C ABI with pinned host buffers
     prm_h = ctx.pipeline_params(Nv=g.Nv, Nr=g.Nr, Nc=g.Nc, Nk=pb.Nk, N=g.N, K=K, nmf_iters=NMF_ITERS,
@@ -248,10 +263,7 @@ def run_ours(args, rank, world, device):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, device)
     if ctx.status(ws_h) != 0:
         raise RuntimeError("device status after end-to-end steps")
 
@@ -289,7 +301,7 @@ def run_ours(args, rank, world, device):
                    "init": "nndsvd", "mbir": "SQS + momentum, qGGMRF p=1.2 q=2 T=1",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (P is 3.54 GB per step)"},
-        "e2e": {"value": world * vb / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": whole_job_value(world, vb, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": "nmf_mma_kernel (fused fast-HALS pass, warp MMA)", "achieved": achieved,
