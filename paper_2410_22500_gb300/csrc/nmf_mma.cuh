@@ -33,6 +33,12 @@
 namespace fhr {
 
 constexpr int kMmaRows = 8;            // pixel rows per tile
+
+// the producer issues a tile's bulk copies from one lane per row (true) or all from lane 0
+template <typename TP>
+struct MmaProducerLanes {
+    static constexpr bool V = sizeof(TP) == 2;
+};
 constexpr int kMmaCW = 13;             // consumer warps (16 warps in all: 128 registers per thread)
 constexpr int kMmaThreads = (kMmaCW + 3) * 32;   // consumers, 2 update warps, producer
 constexpr int kMmaWbStride = 48;       // bytes per s-row of the staged w (conflict-free ldmatrix)
@@ -243,42 +249,63 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     __syncthreads();
 
     if (role == 2) {
-        // ---------------- producer warp: one bulk copy per pixel row
-        if (lane == 0) {
-            int s = 0;
-            uint32_t par = 0;
-            int64_t i = 0;
-            int64_t r0 = (int64_t)blockIdx.x * kMmaRows;
-            const int64_t rstep = (int64_t)gridDim.x * kMmaRows;
-            const uint32_t row_bytes = (uint32_t)((size_t)a.ldP * ES);
-            for (; i < my_tiles; ++i, r0 += rstep) {
-                if (i >= S && !mbar_wait_bounded(&empty[s], par ^ 1u)) {
-                    report(a.status, FHR_ERR_TIMEOUT);
-                    break;
+        // ---------------- producer warp: one bulk copy per pixel row.  With LANES, lane r
+        // issues row r (lane 8 the tile's W rows, lane 9 the L2 prefetch), so a tile's
+        // copies leave in one warp instruction (the gain for the shorter bf16 rows);
+        // otherwise lane 0 alone runs the ring and issues them in turn.
+        constexpr bool LANES = MmaProducerLanes<TP>::V;
+        if (!LANES && lane != 0) return;
+        int s = 0;
+        uint32_t par = 0;
+        int64_t i = 0;
+        int64_t r0 = (int64_t)blockIdx.x * kMmaRows;
+        const int64_t rstep = (int64_t)gridDim.x * kMmaRows;
+        const uint32_t row_bytes = (uint32_t)((size_t)a.ldP * ES);
+        for (; i < my_tiles; ++i, r0 += rstep) {
+            bool ok = true;
+            if (lane == 0 && i >= S) ok = mbar_wait_bounded(&empty[s], par ^ 1u);
+            if constexpr (LANES) ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                if (lane == 0) report(a.status, FHR_ERR_TIMEOUT);
+                break;
+            }
+            const int rows = (int)((a.Np - r0) < kMmaRows ? (a.Np - r0) : kMmaRows);
+            // the W rows of a full tile travel with it (8 K floats: a multiple of 16 bytes)
+            const uint32_t wbytes = (reads_w && rows == kMmaRows) ? (uint32_t)(kMmaRows * K * sizeof(float)) : 0u;
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)rows * row_bytes + wbytes);
+            unsigned char *dst = smem + Lyt.tiles + (size_t)s * stage_bytes;
+            const TP *src = reinterpret_cast<const TP *>(a.P) + r0 * a.ldP;
+            const int64_t rp = r0 + (int64_t)S * rstep;
+            if constexpr (LANES) {
+                __syncwarp();
+                if (lane < rows) {
+                    bulk_g2s(dst + (size_t)lane * RS, src + (size_t)lane * a.ldP, row_bytes, &full[s]);
+                } else if (lane == kMmaRows) {
+                    if (wbytes)
+                        bulk_g2s(smem + Lyt.wst + (size_t)s * kMmaRows * kMaxK * sizeof(float), a.W + r0 * K, wbytes,
+                                 &full[s]);
+                } else if (lane == kMmaRows + 1 && rp < a.Np) {
+                    const int prow = (int)((a.Np - rp) < kMmaRows ? (a.Np - rp) : kMmaRows);
+                    bulk_prefetch_l2(reinterpret_cast<const TP *>(a.P) + rp * a.ldP, (uint32_t)prow * row_bytes);
                 }
-                const int rows = (int)((a.Np - r0) < kMmaRows ? (a.Np - r0) : kMmaRows);
-                // the W rows of a full tile travel with it (8 K floats: a multiple of 16 bytes)
-                const uint32_t wbytes = (reads_w && rows == kMmaRows) ? (uint32_t)(kMmaRows * K * sizeof(float)) : 0u;
-                mbar_arrive_expect_tx(&full[s], (uint32_t)rows * row_bytes + wbytes);
-                const TP *src = reinterpret_cast<const TP *>(a.P) + r0 * a.ldP;
-                unsigned char *dst = smem + Lyt.tiles + (size_t)s * stage_bytes;
+            } else {
                 for (int r = 0; r < rows; ++r) bulk_g2s(dst + (size_t)r * RS, src + (size_t)r * a.ldP, row_bytes, &full[s]);
                 if (wbytes)
                     bulk_g2s(smem + Lyt.wst + (size_t)s * kMmaRows * kMaxK * sizeof(float), a.W + r0 * K, wbytes,
                              &full[s]);
-                const int64_t rp = r0 + (int64_t)S * rstep;
                 if (rp < a.Np) {
                     const int prow = (int)((a.Np - rp) < kMmaRows ? (a.Np - rp) : kMmaRows);
                     bulk_prefetch_l2(reinterpret_cast<const TP *>(a.P) + rp * a.ldP, (uint32_t)prow * row_bytes);
                 }
-                if (++s == S) {
-                    s = 0;
-                    par ^= 1u;
-                }
             }
+            if (++s == S) {
+                s = 0;
+                par ^= 1u;
+            }
+        }
+        if (lane == 0)
             for (int64_t j = (i > S ? i - S : 0); j < i; ++j)
                 if (!mbar_wait_bounded(&full[(int)(j % S)], (uint32_t)((j / S) & 1))) report(a.status, FHR_ERR_TIMEOUT);
-        }
         return;
     }
 
@@ -312,7 +339,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
             const int64_t r0 = (blockIdx.x + i * gridDim.x) * kMmaRows;
             const int rows = (int)((a.Np - r0) < kMmaRows ? (a.Np - r0) : kMmaRows);
             // the tile's W rows arrive with its data: read them before waiting for phase 1
-            if (!mbar_wait_bounded(&full[su], paru)) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[su], paru))) {   // warp-uniform exit
                 report(a.status, FHR_ERR_TIMEOUT);
                 break;
             }
@@ -331,7 +358,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                         if (s < K) w[s] = a.W[(r0 + row) * K + s] * sc[s];
                 }
             }
-            if (!mbar_wait_bounded(&redfull[b], hpar)) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&redfull[b], hpar))) {
                 report(a.status, FHR_ERR_TIMEOUT);
                 break;
             }

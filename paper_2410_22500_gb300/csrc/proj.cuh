@@ -239,6 +239,17 @@ static inline GatherShape gather_shape(int Wl, size_t slab_values, int max_g, in
         if (max_g >= 4 && g.wc % 16 == 0) g.g = 4;
         else if (max_g >= 2 && g.wc % 8 == 0) g.g = 2;
     }
+    // an item's threads: halve the chunk down to `target` where it divides, and never
+    // more than a block (else the largest chunk of whole vectors that fits, one group)
+    while (g.wc / (g.vw * g.g) > target && g.wc % (2 * g.vw * g.g) == 0) g.wc /= 2;
+    if (g.wc / (g.vw * g.g) > 1024) {
+        g.g = 1;
+        for (int c = std::min(Wl, 1024 * g.vw); c >= g.vw; --c)
+            if (Wl % c == 0 && c % g.vw == 0) {
+                g.wc = c;
+                break;
+            }
+    }
     g.ch = g.wc / (g.vw * g.g);
     g.ipb = std::max(1, target / g.ch);
     g.threads = g.ipb * g.ch;

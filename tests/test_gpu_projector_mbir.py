@@ -176,3 +176,25 @@ def test_full_size_projector_pair_and_mbir(fx, orc):
     got = fx.reconstruct(_dev(V), N, Nr, K, 2, momentum=True).cpu().numpy()
     want = orc.mbir(V.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, iters=2, momentum=True)
     assert _rel(got, want) <= 1e-4
+
+
+@pytest.mark.parametrize("Wl", [4096, 4092, 1023, 2056])
+def test_wide_channel_vectors(fx, orc, Wl):
+    # the widest channel vectors the projector takes (1..1024, or multiples of 4 up to
+    # 4096) on a small image, where no L2 chunking splits them: up to 1023 threads per item
+    N, Nc, Nv = 8, 12, 6
+    rng = np.random.default_rng(800 + Wl)
+    x = rng.uniform(0, 1, size=(N, N, Wl)).astype(np.float32)
+    y = fx.project(_dev(x), Nc, Nv).cpu().numpy()
+    assert _rel(y, orc.project(x.astype(np.float64), Nc, _angles(Nv))) <= 1e-5
+    e = rng.normal(size=(Nv, Nc, Wl)).astype(np.float32)
+    xb = fx.backproject(_dev(e), N).cpu().numpy()
+    assert _rel(xb, orc.backproject(e.astype(np.float64), N, _angles(Nv))) <= 1e-5
+
+
+def test_too_wide_channel_vectors_are_rejected(fx):
+    from paper_2410_22500_gb300 import fhr
+
+    for Wl in (4100, 1025):
+        with pytest.raises(fhr.FhrError):
+            fx.project(_dev(np.zeros((8, 8, Wl), np.float32)), 12, 6)
