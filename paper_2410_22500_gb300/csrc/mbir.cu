@@ -82,7 +82,7 @@ __global__ void fill_kernel(float *x, int64_t n, float v) {
 }
 
 template <int VW, int G>
-__global__ void __launch_bounds__(1024) mbir_update_kernel(const float *__restrict__ e, const float *__restrict__ z,
+__global__ void __launch_bounds__(kUpdateThreads, kUpdateMinBlocks) mbir_update_kernel(const float *__restrict__ e, const float *__restrict__ z,
                                                            const float *__restrict__ xprev, float *__restrict__ xnew,
                                                            float *__restrict__ znext, ProjTables t,
                                                            const float *__restrict__ dA, const MbirChan *__restrict__ chp,
@@ -143,7 +143,7 @@ static fhr_status launch_update_g(fhr_ctx *ctx, const fhr_geom *g, const GatherS
 
 static fhr_status launch_update(fhr_ctx *ctx, const fhr_geom *g, const MbirWs &w, const float *z, const float *xp,
                                 float *xn, float *zn, const MbirPrior &pr, float a, int K, int Wl) {
-    const GatherShape s = gather_shape(Wl, gather_slab_values(g), kGatherMaxGBwd);
+    const GatherShape s = gather_shape(Wl, gather_slab_values(g), kGatherMaxGBwd, kUpdateThreads);
     if (s.vw == 4 && s.g == 2) return launch_update_g<4, 2>(ctx, g, s, w, z, xp, xn, zn, pr, a, K, Wl);
     if (s.vw == 4) return launch_update_g<4, 1>(ctx, g, s, w, z, xp, xn, zn, pr, a, K, Wl);
     return launch_update_g<1, 1>(ctx, g, s, w, z, xp, xn, zn, pr, a, K, Wl);

@@ -217,6 +217,9 @@ constexpr size_t kGatherSlab = (size_t)32 << 20;
 // groups per thread: the forward gather gains up to 4 (0.341 -> 0.287 ms on the
 // 128^2 x 64 slice / K = 5 shape), the fused backward + update is best at 2
 constexpr int kGatherMaxGFwd = 4, kGatherMaxGBwd = 2;
+// the fused backward + update is held to 48 registers (five 256-thread blocks per SM:
+// 0.393 -> 0.355 ms on that shape), so its blocks have at most 256 threads
+constexpr int kUpdateThreads = 256, kUpdateMinBlocks = 5;
 
 struct GatherShape {
     int vw, g, wc, ch, ipb, threads;   // g: groups of vw values per thread
@@ -226,7 +229,8 @@ struct GatherShape {
     }
 };
 
-static inline GatherShape gather_shape(int Wl, size_t slab_values, int max_g, int target = 256) {
+static inline GatherShape gather_shape(int Wl, size_t slab_values, int max_g, int max_threads = 1024,
+                                       int target = 256) {
     GatherShape g;
     g.vw = (Wl % 4 == 0) ? 4 : 1;
     g.wc = Wl;
@@ -240,11 +244,12 @@ static inline GatherShape gather_shape(int Wl, size_t slab_values, int max_g, in
         else if (max_g >= 2 && g.wc % 8 == 0) g.g = 2;
     }
     // an item's threads: halve the chunk down to `target` where it divides, and never
-    // more than a block (else the largest chunk of whole vectors that fits, one group)
+    // more than the kernel's block limit (else the largest chunk of whole vectors that
+    // fits, one group)
     while (g.wc / (g.vw * g.g) > target && g.wc % (2 * g.vw * g.g) == 0) g.wc /= 2;
-    if (g.wc / (g.vw * g.g) > 1024) {
+    if (g.wc / (g.vw * g.g) > max_threads) {
         g.g = 1;
-        for (int c = std::min(Wl, 1024 * g.vw); c >= g.vw; --c)
+        for (int c = std::min(Wl, max_threads * g.vw); c >= g.vw; --c)
             if (Wl % c == 0 && c % g.vw == 0) {
                 g.wc = c;
                 break;
