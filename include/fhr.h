@@ -77,7 +77,8 @@ const char *fhr_version(void);
  * those events and returns the number of launches and their summed device
  * time in ms for `name` in {"normalise", "nmf_pass", "nndsvd_pass",
  * "nmf_reduce", "nmf_update", "proj_fwd", "mbir_update", "proj_bwd",
- * "expand"}; with
+ * "expand", "fbp_filter", "mlp_forward" (a whole forward), "fmd" (a whole
+ * fhr_fmd)}; with
  * name == NULL it returns the total launch count since the last enable.
  * "nmf_pass" counts the fused passes of the HALS iterations; the projection
  * passes of the NNDSVD start are counted under "nndsvd_pass". */

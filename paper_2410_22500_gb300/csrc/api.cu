@@ -38,7 +38,7 @@ cudaEvent_t *timer_begin(fhr_ctx *ctx, int id) {
 
 static const char *kTimerNames[TM_COUNT] = {"normalise", "nmf_pass", "nmf_reduce", "nmf_update", "proj_fwd",
                                             "mbir_update", "proj_bwd", "expand", "nndsvd_pass", "fbp_filter",
-                                            "mlp_forward"};
+                                            "mlp_forward", "fmd"};
 
 }  // namespace fhr
 

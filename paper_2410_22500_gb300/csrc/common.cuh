@@ -14,7 +14,7 @@
 // profiling on, launches of the timed kernel families are bracketed by CUDA
 // events on the context's stream (read back by fhr_profile_read).
 enum FhrTimer { TM_NORMALISE = 0, TM_NMF_PASS, TM_NMF_REDUCE, TM_NMF_UPDATE, TM_PROJ_FWD, TM_MBIR_UPDATE,
-                TM_PROJ_BWD, TM_EXPAND, TM_NNDSVD_PASS, TM_FBP_FILTER, TM_MLP_FORWARD, TM_COUNT };
+                TM_PROJ_BWD, TM_EXPAND, TM_NNDSVD_PASS, TM_FBP_FILTER, TM_MLP_FORWARD, TM_FMD, TM_COUNT };
 
 struct fhr_ctx {
     int device;

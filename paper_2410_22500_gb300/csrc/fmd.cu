@@ -217,6 +217,7 @@ extern "C" fhr_status fhr_fmd(fhr_ctx *ctx, int64_t Nx, int Ns, int Nm, int Nk, 
     FHR_ARG(ws_bytes >= need, "workspace too small: %zu < %zu bytes", ws_bytes, need);
     FHR_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
+    cudaEvent_t *ev = timer_begin(ctx, TM_FMD);   // the whole decomposition, when profiling
     FHR_CUDA(cudaMemsetAsync(w.status, 0, kStatusBytes, st));
     fmd_region_partials<<<kFmdBlocks, kFmdMaxM * kFmdMaxS, 0, st>>>(xs, labels, Nx, Ns, Nm, w.part, w.cnt);
     FHR_LAUNCHED();
@@ -226,5 +227,6 @@ extern "C" fhr_status fhr_fmd(fhr_ctx *ctx, int64_t Nx, int Ns, int Nm, int Nk, 
     FHR_LAUNCHED();
     fmd_nnls<<<(unsigned)cdiv(Nx, 128), 128, 0, st>>>(xs, w.T64, w.G, Nx, Ns, Nm, xm);
     FHR_LAUNCHED();
+    if (ev) cudaEventRecord(ev[1], st);
     return FHR_OK;
 }

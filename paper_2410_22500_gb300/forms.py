@@ -4,6 +4,7 @@ line per case; device timing with CUDA events on the library's stream).
     python -m paper_2410_22500_gb300.forms precision
     python -m paper_2410_22500_gb300.forms batched [n_problems] [iters]
     python -m paper_2410_22500_gb300.forms learned [n_train]
+    python -m paper_2410_22500_gb300.forms fbp_fmd
 
 `precision`: the 256^3 volume (6 ellipsoids, Nk = 1500, 120 views, 256 x 256
 detector, 100 counts per bin; P is 7.86M x 1500) through Algorithm 1 with P
@@ -33,6 +34,14 @@ FP32 P.  Reports iterations, whole-pipeline times and the speedup; also the
 plain form stopped at the iteration where it first came within 1e-3 of its own
 final objective, and the BF16 form from the NNDSVD start with the fewest
 iterations that reach the same target (what the learned start adds to BF16).
+
+`fbp_fmd`: the 3-D f32 workload (the benchmark's) through Algorithm 1 with the
+MBIR and with the FBP reconstruction (200 NMF iterations; 100 SQS iterations),
+whole-pipeline times and the FBP kernels' times; then the semi-supervised FMD
+(Algorithm 2 after the reconstruction) of its MBIR subspace volume with the
+phantom's pure voxels as the user regions: the time of fhr_fmd, its HBM rate
+against the algorithmic bytes, and the relative error of each estimated
+material spectrum D^m against the phantom's over the live bins.
 """
 import ctypes
 import json
@@ -280,10 +289,67 @@ def learned(n_train: int = 12) -> None:
     ctx.close()
 
 
+def fbp_fmd() -> None:
+    build.build()
+    ctx = fhr.Context(0)
+    pb = synth.volume_3d_f32()
+    g = pb.geom
+    K = 5
+    y, y0 = synth.counts_torch(pb, device="cuda")
+    dead = torch.from_numpy(pb.dead_bins).cuda()
+    D = torch.empty((pb.Nk, K), dtype=torch.float32, device="cuda")
+    xh = torch.empty((g.Nr, g.N, g.N, pb.Nk), dtype=torch.float32, device="cuda")
+    vb = g.Nr * g.N * g.N * pb.Nk
+    out = {"case": "fbp_fmd", "workload": "128x128x64 volume, Nk=1200, 90 views, 64x128 detector, K=5"}
+    for name, recon in (("mbir", fhr.RECON_MBIR), ("fbp", fhr.RECON_FBP)):
+        prm = ctx.pipeline_params(Nv=g.Nv, Nr=g.Nr, Nc=g.Nc, Nk=pb.Nk, N=g.N, K=K, nmf_iters=NMF_ITERS,
+                                  mbir_iters=MBIR_ITERS, momentum=True, seed=17, recon=recon)
+        ws, wsb = ctx.pipeline_workspace(prm)
+        run = lambda: ctx.pipeline(prm, y, y0, D, xh, dead=dead, ws=ws, ws_bytes=wsb)
+        run()
+        ctx.check(ctx.status(ws))
+        ctx.profile(True)
+        ms = _timed(ctx, run)
+        fams = {k: round(ctx.profile_read(k)[1], 3) for k in ("nmf_pass", "proj_fwd", "mbir_update", "fbp_filter",
+                                                              "proj_bwd", "expand")}
+        ctx.profile(False)
+        ctx.check(ctx.status(ws))
+        out["pipeline_" + name] = {"ms": round(ms, 2), "voxel_bins_per_s": vb / (ms / 1e3), "kernel_ms": fams}
+        del ws
+        torch.cuda.empty_cache()
+    # FMD of the MBIR subspace volume, the phantom's pure voxels as the user regions
+    P = ctx.normalise(y, y0, dead=dead)
+    Ds, W, _ = ctx.decompose(P, pb.Nk, K, NMF_ITERS, init=fhr.INIT_NNDSVD, obj=False)
+    del P
+    xs = ctx.reconstruct(W.view(g.Nv, g.Nc, g.Nr * K), g.N, g.Nr, K, MBIR_ITERS, momentum=True)
+    frac = synth.volume_fractions(pb.phantom, g.N, g.Nr)             # [Nr][N][N][Nm]
+    Nm = frac.shape[-1]
+    lab = np.where(frac.max(axis=-1) >= 0.999, frac.argmax(axis=-1) + 1, 0).astype(np.uint8)
+    labels = torch.from_numpy(np.ascontiguousarray(lab.transpose(1, 2, 0))).cuda()   # voxel order (iy, ix, r)
+    T, xm, Dm = ctx.fmd(xs, labels, Ds, Nm)
+    ctx.profile(True)
+    ms = _timed(ctx, lambda: ctx.fmd(xs, labels, Ds, Nm, check_status=False))
+    n_fmd, fmd_ms = ctx.profile_read("fmd")
+    ctx.profile(False)
+    Nx = g.N * g.N * g.Nr
+    nbytes = 2 * Nx * K * 4 + 2 * Nx + Nx * Nm * 4      # x^s twice, labels twice, x^m once
+    live = pb.dead_bins == 0
+    Dm_h = Dm.cpu().numpy().astype(np.float64)[live]
+    mu = pb.spectra[live]
+    err = [float(np.linalg.norm(Dm_h[:, m] - mu[:, m]) / np.linalg.norm(mu[:, m])) for m in range(Nm)]
+    out["fmd"] = {"voxels": Nx, "Ns": K, "Nm": Nm, "labelled_voxels": int((lab > 0).sum()),
+                  "ms": round(fmd_ms / max(n_fmd, 1), 4), "gbs": round(nbytes / (fmd_ms / max(n_fmd, 1) / 1e3) / 1e9, 1),
+                  "algorithmic_bytes": nbytes, "Dm_rel_err_per_material": [round(e, 4) for e in err]}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "precision"
     if case == "precision":
         precision()
+    elif case == "fbp_fmd":
+        fbp_fmd()
     elif case == "learned":
         learned(int(sys.argv[2]) if len(sys.argv) > 2 else 12)
     elif case == "batched":
