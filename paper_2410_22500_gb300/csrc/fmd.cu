@@ -7,14 +7,16 @@
 // Region sums: one block per voxel range, one thread per (region, channel),
 // voxels in order, then a fixed-order sum of the block partials in FP64.  The
 // per-voxel problems: one thread each, Lawson-Hanson active sets on the normal
-// equations (T T^T) x = T x^s_n in FP64 (at most 8 materials).
+// equations (T T^T) x = T x^s_n in FP64 (at most 8 materials), with the inverse of
+// every principal block of T T^T formed once per call.
 #include "common.cuh"
 
 namespace fhr {
 
 constexpr int kFmdMaxM = 8;
 constexpr int kFmdMaxS = 16;
-constexpr int kFmdBlocks = 512;
+constexpr int kFmdBlocks = 2048;
+constexpr int kFmdInvSmem = 4096;   // doubles of subset inverses kept in shared memory (32 KB)
 
 __global__ void fmd_region_partials(const float *__restrict__ xs, const uint8_t *__restrict__ lab, int64_t Nx, int Ns,
                                     int Nm, double *part, long long *cnt) {
@@ -36,32 +38,40 @@ __global__ void fmd_region_partials(const float *__restrict__ xs, const uint8_t 
     }
 }
 
-// T (FP64 and FP32), the Gram G = T T^T, and a status when a region is empty
-__global__ void fmd_finish(const double *part, const long long *cnt, int nb, int Ns, int Nm, double *T64, float *T,
-                           double *G, int *status) {
-    __shared__ double ts[kFmdMaxM * kFmdMaxS];
-    const int t = threadIdx.x;
-    if (t < Nm * Ns) {
-        const int i = t / Ns, j = t % Ns;
-        double s = 0.0;
-        long long c = 0;
-        for (int b = 0; b < nb; ++b) {
-            s += part[((size_t)b * Nm + i) * Ns + j];
-            c += cnt[(size_t)b * Nm + i];
-        }
+// T[i][j] from the block partials, one warp per (region i, channel j): lanes take
+// the blocks in a fixed stride, then a fixed shuffle tree (deterministic); FP32
+// and FP64 copies; a status when a region is empty
+__global__ void fmd_finish_T(const double *part, const long long *cnt, int nb, int Ns, int Nm, double *T64,
+                             float *T, int *status) {
+    const int t = blockIdx.x, lane = threadIdx.x;
+    const int i = t / Ns, j = t % Ns;
+    double s = 0.0;
+    long long c = 0;
+    for (int b = lane; b < nb; b += 32) {
+        s += part[((size_t)b * Nm + i) * Ns + j];
+        c += cnt[(size_t)b * Nm + i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
         const double v = c > 0 ? s / (double)c : 0.0;
         if (c == 0 && j == 0) report(status, FHR_ERR_ARG);
-        ts[t] = v;
         T64[t] = v;
         T[t] = (float)v;
     }
-    __syncthreads();
-    if (t < Nm * Nm) {
-        const int a = t / Nm, b = t % Nm;
-        double g = 0.0;
-        for (int j = 0; j < Ns; ++j) g += ts[a * Ns + j] * ts[b * Ns + j];
-        G[t] = g;
-    }
+}
+
+// G = T T^T (FP64)
+__global__ void fmd_gram(const double *T64, int Ns, int Nm, double *G) {
+    const int t = threadIdx.x;
+    if (t >= Nm * Nm) return;
+    const int a = t / Nm, b = t % Nm;
+    double g = 0.0;
+    for (int j = 0; j < Ns; ++j) g += T64[a * Ns + j] * T64[b * Ns + j];
+    G[t] = g;
 }
 
 __global__ void fmd_spectra(const float *__restrict__ D, const double *__restrict__ T64, int Nk, int Ns, int Nm,
@@ -74,43 +84,77 @@ __global__ void fmd_spectra(const float *__restrict__ D, const double *__restric
     Dm[idx] = (float)s;
 }
 
-// z_P = G_PP^-1 b_P by Cholesky (FP64), z = 0 outside P; false if not positive definite
-__device__ bool fmd_solve(const double *G, const double *b, int Nm, unsigned P, double *z) {
+// Every active set P of the per-voxel problems shares G = T T^T, so the inverse of
+// each principal block G_PP (at most 2^8 of them) is formed once, in FP64, one
+// thread per subset: Cholesky of G_PP, then its inverse embedded in an Nm x Nm
+// block with zeros outside P.  inv[P * Nm * Nm] = NaN marks a block that is not
+// positive definite.
+__global__ void fmd_subset_inverses(const double *__restrict__ Gg, int Nm, double *inv) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= (1 << Nm)) return;
+    double *out = inv + (size_t)P * Nm * Nm;
+    for (int i = 0; i < Nm * Nm; ++i) out[i] = 0.0;
     int idx[kFmdMaxM], m = 0;
     for (int i = 0; i < Nm; ++i)
-        if (P >> i & 1u) idx[m++] = i;
-    double L[kFmdMaxM * kFmdMaxM], y[kFmdMaxM];
+        if (P >> i & 1) idx[m++] = i;
+    double L[kFmdMaxM * kFmdMaxM];
     for (int r = 0; r < m; ++r) {
         for (int c = 0; c <= r; ++c) {
-            double s = G[idx[r] * Nm + idx[c]];
+            double s = Gg[idx[r] * Nm + idx[c]];
             for (int k = 0; k < c; ++k) s -= L[r * kFmdMaxM + k] * L[c * kFmdMaxM + k];
             if (r == c) {
-                if (!(s > 0.0)) return false;
+                if (!(s > 0.0)) {
+                    out[0] = nan("");
+                    return;
+                }
                 L[r * kFmdMaxM + r] = sqrt(s);
             } else {
                 L[r * kFmdMaxM + c] = s / L[c * kFmdMaxM + c];
             }
         }
     }
-    for (int r = 0; r < m; ++r) {
-        double s = b[idx[r]];
-        for (int k = 0; k < r; ++k) s -= L[r * kFmdMaxM + k] * y[k];
-        y[r] = s / L[r * kFmdMaxM + r];
+    // column e of the inverse: L y = e_e, then L^T z = y
+    for (int e = 0; e < m; ++e) {
+        double y[kFmdMaxM], z[kFmdMaxM];
+        for (int r = 0; r < m; ++r) {
+            double s = r == e ? 1.0 : 0.0;
+            for (int k = 0; k < r; ++k) s -= L[r * kFmdMaxM + k] * y[k];
+            y[r] = s / L[r * kFmdMaxM + r];
+        }
+        for (int r = m - 1; r >= 0; --r) {
+            double s = y[r];
+            for (int k = r + 1; k < m; ++k) s -= L[k * kFmdMaxM + r] * z[k];
+            z[r] = s / L[r * kFmdMaxM + r];
+        }
+        for (int r = 0; r < m; ++r) out[idx[r] * Nm + idx[e]] = z[r];
     }
-    for (int i = 0; i < Nm; ++i) z[i] = 0.0;
-    for (int r = m - 1; r >= 0; --r) {
-        double s = y[r];
-        for (int k = r + 1; k < m; ++k) s -= L[k * kFmdMaxM + r] * z[idx[k]];
-        z[idx[r]] = s / L[r * kFmdMaxM + r];
+}
+
+// z = G_PP^-1 b_P (zero outside P) from the table; false if G_PP is not positive definite
+__device__ __forceinline__ bool fmd_solve(const double *inv, const double *b, int Nm, unsigned P, double *z) {
+    const double *S = inv + (size_t)P * Nm * Nm;
+    if (isnan(S[0])) return false;
+    for (int i = 0; i < Nm; ++i) {
+        double s = 0.0;
+        if (P >> i & 1u)
+            for (int k = 0; k < Nm; ++k)
+                if (P >> k & 1u) s = fma(S[i * Nm + k], b[k], s);
+        z[i] = s;
     }
     return true;
 }
 
 __global__ void fmd_nnls(const float *__restrict__ xs, const double *__restrict__ T64, const double *__restrict__ Gg,
-                         int64_t Nx, int Ns, int Nm, float *xm) {
+                         const double *__restrict__ inv_g, int64_t Nx, int Ns, int Nm, float *xm) {
+    extern __shared__ double fmd_sm[];   // the subset inverses, when they fit (else read from global)
     __shared__ double G[kFmdMaxM * kFmdMaxM], T[kFmdMaxM * kFmdMaxS];
     for (int i = threadIdx.x; i < Nm * Nm; i += blockDim.x) G[i] = Gg[i];
     for (int i = threadIdx.x; i < Nm * Ns; i += blockDim.x) T[i] = T64[i];
+    const int ninv = (1 << Nm) * Nm * Nm;
+    const bool in_smem = ninv <= kFmdInvSmem;
+    if (in_smem)
+        for (int i = threadIdx.x; i < ninv; i += blockDim.x) fmd_sm[i] = inv_g[i];
+    const double *inv = in_smem ? fmd_sm : inv_g;
     __syncthreads();
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= Nx) return;
@@ -142,7 +186,7 @@ __global__ void fmd_nnls(const float *__restrict__ xs, const double *__restrict_
         if (t < 0) break;
         P |= 1u << t;
         for (int inner = 0; inner < 3 * kFmdMaxM; ++inner) {
-            if (!fmd_solve(G, b, Nm, P, z)) {
+            if (!fmd_solve(inv, b, Nm, P, z)) {
                 P &= ~(1u << t);
                 break;
             }
@@ -170,7 +214,7 @@ __global__ void fmd_nnls(const float *__restrict__ xs, const double *__restrict_
 
 struct FmdWs {
     int *status;
-    double *part, *T64, *G;
+    double *part, *T64, *G, *inv;
     long long *cnt;
 };
 
@@ -182,6 +226,7 @@ static size_t carve_fmd(void *base, int Ns, int Nm, FmdWs *w) {
     t.cnt = c.take<long long>((size_t)kFmdBlocks * Nm);
     t.T64 = c.take<double>((size_t)Nm * Ns);
     t.G = c.take<double>((size_t)Nm * Nm);
+    t.inv = c.take<double>((size_t)(1 << Nm) * Nm * Nm);
     if (w) *w = t;
     return c.size();
 }
@@ -221,11 +266,17 @@ extern "C" fhr_status fhr_fmd(fhr_ctx *ctx, int64_t Nx, int Ns, int Nm, int Nk, 
     FHR_CUDA(cudaMemsetAsync(w.status, 0, kStatusBytes, st));
     fmd_region_partials<<<kFmdBlocks, kFmdMaxM * kFmdMaxS, 0, st>>>(xs, labels, Nx, Ns, Nm, w.part, w.cnt);
     FHR_LAUNCHED();
-    fmd_finish<<<1, kFmdMaxM * kFmdMaxS, 0, st>>>(w.part, w.cnt, kFmdBlocks, Ns, Nm, w.T64, T, w.G, w.status);
+    fmd_finish_T<<<Nm * Ns, 32, 0, st>>>(w.part, w.cnt, kFmdBlocks, Ns, Nm, w.T64, T, w.status);
+    FHR_LAUNCHED();
+    fmd_gram<<<1, kFmdMaxM * kFmdMaxM, 0, st>>>(w.T64, Ns, Nm, w.G);
     FHR_LAUNCHED();
     fmd_spectra<<<(unsigned)cdiv((int64_t)Nk * Nm, 256), 256, 0, st>>>(D, w.T64, Nk, Ns, Nm, Dm);
     FHR_LAUNCHED();
-    fmd_nnls<<<(unsigned)cdiv(Nx, 128), 128, 0, st>>>(xs, w.T64, w.G, Nx, Ns, Nm, xm);
+    fmd_subset_inverses<<<(unsigned)cdiv(1 << Nm, 64), 64, 0, st>>>(w.G, Nm, w.inv);
+    FHR_LAUNCHED();
+    const int ninv = (1 << Nm) * Nm * Nm;
+    const size_t smem = ninv <= kFmdInvSmem ? (size_t)ninv * sizeof(double) : 0;
+    fmd_nnls<<<(unsigned)cdiv(Nx, 128), 128, smem, st>>>(xs, w.T64, w.G, w.inv, Nx, Ns, Nm, xm);
     FHR_LAUNCHED();
     if (ev) cudaEventRecord(ev[1], st);
     return FHR_OK;
