@@ -1,6 +1,7 @@
 // Instantiations and launch configuration of the fused NMF pass: the
-// tensor-core kernel (nmf_mma.cuh) up to 1536 (f32) / 2112 (bf16) bins per
-// row, the CUDA-core kernel (nmf_pass.cuh) beyond.
+// tensor-core kernel (nmf_mma.cuh) up to 1664 (f32) / 2288 (bf16) bins per
+// row (13 consumer warps x 128 / 176 bins), the CUDA-core kernel
+// (nmf_pass.cuh) beyond.
 #include "nmf_internal.h"
 #include "nmf_mma.cuh"
 #include "nmf_pass.cuh"
