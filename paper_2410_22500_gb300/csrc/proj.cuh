@@ -266,7 +266,6 @@ static inline size_t gather_slab_values(const fhr_geom *g) {
     return std::max((size_t)g->N * g->N, (size_t)g->Nv * g->Nc);
 }
 
-size_t proj_tables_bytes(int N, int Nc, int Nv);
 void proj_tables_carve(Carve &c, int N, int Nc, int Nv, ProjTables *t);
 fhr_status proj_build_tables(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t);
 fhr_status proj_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *x, float *y,

@@ -8,8 +8,8 @@ unique only up to order and scale, so every training decomposition is put in a
 canonical form first: D's columns are unit L2 (the decomposition already does
 this) and are ordered by best cosine match to the library's spectra.  The
 network then predicts W in that canonical basis, and FHR_INIT_LEARNED starts
-the iterations from it.  The plain iterations remain the method and the judge
-of the result: the warm start only changes where they begin.
+the iterations from it.  The plain iterations remain the method and decide
+the result: the warm start only changes where they begin.
 """
 from __future__ import annotations
 
