@@ -16,7 +16,7 @@ namespace fhr {
 constexpr int kFmdMaxM = 8;
 constexpr int kFmdMaxS = 16;
 constexpr int kFmdBlocks = 2048;
-constexpr int kFmdInvSmem = 4096;   // doubles of subset inverses kept in shared memory (32 KB)
+constexpr int kFmdInvSmem = 2304;   // subset inverses kept in shared memory (FP64 + FP32: 27 KB, Nm <= 6)
 
 __global__ void fmd_region_partials(const float *__restrict__ xs, const uint8_t *__restrict__ lab, int64_t Nx, int Ns,
                                     int Nm, double *part, long long *cnt) {
@@ -27,11 +27,21 @@ __global__ void fmd_region_partials(const float *__restrict__ xs, const uint8_t 
     double s = 0.0;
     long long c = 0;
     if (i < Nm) {
-        for (int64_t n = lo; n < hi; ++n) {
-            if (lab[n] == i + 1) {
-                s += (double)xs[n * Ns + j];
-                ++c;
-            }
+        // eight voxels per step, their loads issued together; summed in voxel order
+        constexpr int U = 8;
+        for (int64_t n0 = lo; n0 < hi; n0 += U) {
+            int lb[U];
+            float v[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) lb[k] = n0 + k < hi ? lab[n0 + k] : 0;
+#pragma unroll
+            for (int k = 0; k < U; ++k) v[k] = lb[k] == i + 1 ? xs[(n0 + k) * Ns + j] : 0.f;
+#pragma unroll
+            for (int k = 0; k < U; ++k)
+                if (lb[k] == i + 1) {
+                    s += (double)v[k];
+                    ++c;
+                }
         }
         part[((size_t)blockIdx.x * Nm + i) * Ns + j] = s;
         if (j == 0) cnt[(size_t)blockIdx.x * Nm + i] = c;
@@ -89,10 +99,11 @@ __global__ void fmd_spectra(const float *__restrict__ D, const double *__restric
 // thread per subset: Cholesky of G_PP, then its inverse embedded in an Nm x Nm
 // block with zeros outside P.  inv[P * Nm * Nm] = NaN marks a block that is not
 // positive definite.
-__global__ void fmd_subset_inverses(const double *__restrict__ Gg, int Nm, double *inv) {
+__global__ void fmd_subset_inverses(const double *__restrict__ Gg, int Nm, double *inv, float *invf) {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= (1 << Nm)) return;
     double *out = inv + (size_t)P * Nm * Nm;
+    float *outf = invf + (size_t)P * Nm * Nm;
     for (int i = 0; i < Nm * Nm; ++i) out[i] = 0.0;
     int idx[kFmdMaxM], m = 0;
     for (int i = 0; i < Nm; ++i)
@@ -105,6 +116,7 @@ __global__ void fmd_subset_inverses(const double *__restrict__ Gg, int Nm, doubl
             if (r == c) {
                 if (!(s > 0.0)) {
                     out[0] = nan("");
+                    for (int i = 0; i < Nm * Nm; ++i) outf[i] = i == 0 ? nanf("") : 0.f;
                     return;
                 }
                 L[r * kFmdMaxM + r] = sqrt(s);
@@ -128,14 +140,16 @@ __global__ void fmd_subset_inverses(const double *__restrict__ Gg, int Nm, doubl
         }
         for (int r = 0; r < m; ++r) out[idx[r] * Nm + idx[e]] = z[r];
     }
+    for (int i = 0; i < Nm * Nm; ++i) outf[i] = (float)out[i];
 }
 
 // z = G_PP^-1 b_P (zero outside P) from the table; false if G_PP is not positive definite
-__device__ __forceinline__ bool fmd_solve(const double *inv, const double *b, int Nm, unsigned P, double *z) {
-    const double *S = inv + (size_t)P * Nm * Nm;
+template <typename R>
+__device__ __forceinline__ bool fmd_solve(const R *inv, const R *b, int Nm, unsigned P, R *z) {
+    const R *S = inv + (size_t)P * Nm * Nm;
     if (isnan(S[0])) return false;
     for (int i = 0; i < Nm; ++i) {
-        double s = 0.0;
+        R s = 0;
         if (P >> i & 1u)
             for (int k = 0; k < Nm; ++k)
                 if (P >> k & 1u) s = fma(S[i * Nm + k], b[k], s);
@@ -144,39 +158,19 @@ __device__ __forceinline__ bool fmd_solve(const double *inv, const double *b, in
     return true;
 }
 
-__global__ void fmd_nnls(const float *__restrict__ xs, const double *__restrict__ T64, const double *__restrict__ Gg,
-                         const double *__restrict__ inv_g, int64_t Nx, int Ns, int Nm, float *xm) {
-    extern __shared__ double fmd_sm[];   // the subset inverses, when they fit (else read from global)
-    __shared__ double G[kFmdMaxM * kFmdMaxM], T[kFmdMaxM * kFmdMaxS];
-    for (int i = threadIdx.x; i < Nm * Nm; i += blockDim.x) G[i] = Gg[i];
-    for (int i = threadIdx.x; i < Nm * Ns; i += blockDim.x) T[i] = T64[i];
-    const int ninv = (1 << Nm) * Nm * Nm;
-    const bool in_smem = ninv <= kFmdInvSmem;
-    if (in_smem)
-        for (int i = threadIdx.x; i < ninv; i += blockDim.x) fmd_sm[i] = inv_g[i];
-    const double *inv = in_smem ? fmd_sm : inv_g;
-    __syncthreads();
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= Nx) return;
-    double b[kFmdMaxM], x[kFmdMaxM], z[kFmdMaxM];
-    double bn = 0.0;
-    for (int i = 0; i < Nm; ++i) {
-        double s = 0.0;
-        for (int j = 0; j < Ns; ++j) s += T[i * Ns + j] * (double)xs[n * Ns + j];
-        b[i] = s;
-        x[i] = 0.0;
-        bn = fmax(bn, fabs(s));
-    }
-    double gmax = 0.0;
-    for (int i = 0; i < Nm * Nm; ++i) gmax = fmax(gmax, fabs(G[i]));
-    const double tol = 1e-13 * fmax(bn, 1e-300) * fmax(1.0, gmax);
+// Lawson-Hanson active-set NNLS on the normal equations G x = b in precision R;
+// returns the final passive set, x holds the solution
+template <typename R>
+__device__ unsigned fmd_lh(const R *G, const R *inv, const R *b, int Nm, R tol, R *x) {
+    R z[kFmdMaxM];
+    for (int i = 0; i < Nm; ++i) x[i] = 0;
     unsigned P = 0;
     for (int outer = 0; outer < 3 * kFmdMaxM; ++outer) {
         // w = b - G x: the most violated coordinate outside P enters
         int t = -1;
-        double best = tol;
+        R best = tol;
         for (int i = 0; i < Nm; ++i) {
-            double s = b[i];
+            R s = b[i];
             for (int k = 0; k < Nm; ++k) s -= G[i * Nm + k] * x[k];
             if (!(P >> i & 1u) && s > best) {
                 best = s;
@@ -186,35 +180,104 @@ __global__ void fmd_nnls(const float *__restrict__ xs, const double *__restrict_
         if (t < 0) break;
         P |= 1u << t;
         for (int inner = 0; inner < 3 * kFmdMaxM; ++inner) {
-            if (!fmd_solve(inv, b, Nm, P, z)) {
+            if (!fmd_solve<R>(inv, b, Nm, P, z)) {
                 P &= ~(1u << t);
                 break;
             }
             bool feasible = true;
             for (int i = 0; i < Nm; ++i)
-                if ((P >> i & 1u) && z[i] <= 0.0) feasible = false;
+                if ((P >> i & 1u) && z[i] <= 0) feasible = false;
             if (feasible) {
                 for (int i = 0; i < Nm; ++i) x[i] = z[i];
                 break;
             }
-            double alpha = 1.0;
+            R alpha = 1;
             for (int i = 0; i < Nm; ++i)
-                if ((P >> i & 1u) && z[i] <= 0.0) alpha = fmin(alpha, x[i] / (x[i] - z[i]));
+                if ((P >> i & 1u) && z[i] <= 0) alpha = fmin(alpha, x[i] / (x[i] - z[i]));
             for (int i = 0; i < Nm; ++i) {
                 x[i] += alpha * (z[i] - x[i]);
-                if ((P >> i & 1u) && x[i] <= 0.0) {
-                    x[i] = 0.0;
+                if ((P >> i & 1u) && x[i] <= 0) {
+                    x[i] = 0;
                     P &= ~(1u << i);
                 }
             }
         }
     }
+    return P;
+}
+
+// Per voxel: the passive set is searched in FP32, then the solution on that set is
+// formed in FP64 and accepted only if it satisfies the NNLS optimality conditions in
+// FP64 (positive on the set, w = b - G x <= tol off it); otherwise the search is
+// repeated in FP64.  The result is the FP64 Lawson-Hanson solution either way.
+__global__ void fmd_nnls(const float *__restrict__ xs, const double *__restrict__ T64, const double *__restrict__ Gg,
+                         const double *__restrict__ inv_g, const float *__restrict__ inv_f, int64_t Nx, int Ns, int Nm,
+                         float *xm) {
+    extern __shared__ double fmd_sm[];   // the subset inverses (FP64, then FP32), when they fit
+    __shared__ double G[kFmdMaxM * kFmdMaxM], T[kFmdMaxM * kFmdMaxS];
+    __shared__ float Gf[kFmdMaxM * kFmdMaxM], Tf[kFmdMaxM * kFmdMaxS];
+    for (int i = threadIdx.x; i < Nm * Nm; i += blockDim.x) {
+        G[i] = Gg[i];
+        Gf[i] = (float)Gg[i];
+    }
+    for (int i = threadIdx.x; i < Nm * Ns; i += blockDim.x) {
+        T[i] = T64[i];
+        Tf[i] = (float)T64[i];
+    }
+    const int ninv = (1 << Nm) * Nm * Nm;
+    const bool in_smem = ninv <= kFmdInvSmem;
+    float *fsm = reinterpret_cast<float *>(fmd_sm + ninv);
+    if (in_smem)
+        for (int i = threadIdx.x; i < ninv; i += blockDim.x) {
+            fmd_sm[i] = inv_g[i];
+            fsm[i] = inv_f[i];
+        }
+    const double *inv = in_smem ? fmd_sm : inv_g;
+    const float *invf = in_smem ? fsm : inv_f;
+    __syncthreads();
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= Nx) return;
+    float v[kFmdMaxS];
+    for (int j = 0; j < Ns; ++j) v[j] = xs[n * Ns + j];
+    double b[kFmdMaxM], x[kFmdMaxM];
+    float bf[kFmdMaxM], xf[kFmdMaxM];
+    double bn = 0.0;
+    float bnf = 0.f;
+    for (int i = 0; i < Nm; ++i) {
+        double s = 0.0;
+        float sf = 0.f;
+        for (int j = 0; j < Ns; ++j) {
+            s += T[i * Ns + j] * (double)v[j];
+            sf = fmaf(Tf[i * Ns + j], v[j], sf);
+        }
+        b[i] = s;
+        bf[i] = sf;
+        bn = fmax(bn, fabs(s));
+        bnf = fmaxf(bnf, fabsf(sf));
+    }
+    double gmax = 0.0;
+    for (int i = 0; i < Nm * Nm; ++i) gmax = fmax(gmax, fabs(G[i]));
+    const double tol = 1e-13 * fmax(bn, 1e-300) * fmax(1.0, gmax);
+    const float tolf = 1e-5f * fmaxf(bnf, 1e-30f) * fmaxf(1.f, (float)gmax);
+    const unsigned P = fmd_lh<float>(Gf, invf, bf, Nm, tolf, xf);
+    bool ok = fmd_solve<double>(inv, b, Nm, P, x);
+    for (int i = 0; i < Nm && ok; ++i) {
+        if (P >> i & 1u) {
+            ok = x[i] > 0.0;
+        } else {
+            double w = b[i];
+            for (int k = 0; k < Nm; ++k) w -= G[i * Nm + k] * x[k];
+            ok = w <= tol;
+        }
+    }
+    if (!ok) fmd_lh<double>(G, inv, b, Nm, tol, x);
     for (int i = 0; i < Nm; ++i) xm[n * Nm + i] = (float)x[i];
 }
 
 struct FmdWs {
     int *status;
     double *part, *T64, *G, *inv;
+    float *invf;
     long long *cnt;
 };
 
@@ -227,6 +290,7 @@ static size_t carve_fmd(void *base, int Ns, int Nm, FmdWs *w) {
     t.T64 = c.take<double>((size_t)Nm * Ns);
     t.G = c.take<double>((size_t)Nm * Nm);
     t.inv = c.take<double>((size_t)(1 << Nm) * Nm * Nm);
+    t.invf = c.take<float>((size_t)(1 << Nm) * Nm * Nm);
     if (w) *w = t;
     return c.size();
 }
@@ -272,11 +336,11 @@ extern "C" fhr_status fhr_fmd(fhr_ctx *ctx, int64_t Nx, int Ns, int Nm, int Nk, 
     FHR_LAUNCHED();
     fmd_spectra<<<(unsigned)cdiv((int64_t)Nk * Nm, 256), 256, 0, st>>>(D, w.T64, Nk, Ns, Nm, Dm);
     FHR_LAUNCHED();
-    fmd_subset_inverses<<<(unsigned)cdiv(1 << Nm, 64), 64, 0, st>>>(w.G, Nm, w.inv);
+    fmd_subset_inverses<<<(unsigned)cdiv(1 << Nm, 64), 64, 0, st>>>(w.G, Nm, w.inv, w.invf);
     FHR_LAUNCHED();
     const int ninv = (1 << Nm) * Nm * Nm;
-    const size_t smem = ninv <= kFmdInvSmem ? (size_t)ninv * sizeof(double) : 0;
-    fmd_nnls<<<(unsigned)cdiv(Nx, 128), 128, smem, st>>>(xs, w.T64, w.G, w.inv, Nx, Ns, Nm, xm);
+    const size_t smem = ninv <= kFmdInvSmem ? (size_t)ninv * (sizeof(double) + sizeof(float)) : 0;
+    fmd_nnls<<<(unsigned)cdiv(Nx, 128), 128, smem, st>>>(xs, w.T64, w.G, w.inv, w.invf, Nx, Ns, Nm, xm);
     FHR_LAUNCHED();
     if (ev) cudaEventRecord(ev[1], st);
     return FHR_OK;
