@@ -3,6 +3,8 @@
     python -m paper_2410_22500_gb300.profcase nmf_pass [Np]
     python -m paper_2410_22500_gb300.profcase nmf_pass_bf16 [Np]
     python -m paper_2410_22500_gb300.profcase mbir
+    python -m paper_2410_22500_gb300.profcase fmd
+    python -m paper_2410_22500_gb300.profcase fbp
 
 `nmf_pass`: P of Np x 1200 uniform f32 (default Np = 92,160: 442 MB, larger than
 L2), K = 5, three fast-HALS iterations from a fixed start.  Launch 0 is the first
@@ -16,6 +18,14 @@ K = 6, the row length and K of the 256^3 precision form.
 64 slices x K = 5, 90 views x 128 bins; uniform random sinogram), four SQS
 iterations with momentum: launches of proj_fwd_kernel and mbir_update_kernel
 at the benchmark's shapes (profile with `-k regex:"proj_fwd|mbir_update" -s 2 -c 2`).
+`fmd`: the semi-supervised material decomposition of 1,048,576 voxels (the 3-D
+workload's volume), Ns = Nm = 5, seeded mixtures with 10% of the voxels labelled,
+Nk = 1200; three calls (fmd_region_partials, fmd_finish_T, fmd_gram, fmd_spectra,
+fmd_subset_inverses, fmd_nnls each).
+
+`fbp`: FBP of the 3-D workload's subspace sinograms (N = 128, 64 slices x K = 5, 90
+views x 128 bins; uniform random sinogram), three calls (fbp_filter_kernel, then
+proj_bwd_kernel each).
 """
 import sys
 
@@ -51,6 +61,41 @@ def mbir(iters: int = 4) -> None:
     print("ok")
 
 
+def fmd(calls: int = 3) -> None:
+    import numpy as np
+
+    build.build()
+    ctx = fhr.Context(0)
+    rng = np.random.default_rng(0)
+    Nx, Ns, Nm, Nk = 1048576, 5, 5, 1200
+    B = rng.normal(size=(Nm, Ns)) + 3 * np.eye(Nm, Ns)
+    xm = rng.uniform(size=(Nx, Nm)) * (rng.uniform(size=(Nx, Nm)) > 0.4)
+    xs = torch.from_numpy((xm @ B + 0.05 * rng.normal(size=(Nx, Ns))).astype(np.float32)).cuda()
+    lab = (np.argmax(xm, axis=1) + 1).astype(np.uint8)
+    lab[rng.uniform(size=Nx) < 0.9] = 0
+    labels = torch.from_numpy(lab).cuda()
+    D = torch.from_numpy(rng.uniform(size=(Nk, Ns)).astype(np.float32)).cuda()
+    for _ in range(calls):
+        ctx.fmd(xs, labels, D, Nm)
+    torch.cuda.synchronize()
+    ctx.close()
+    print("ok")
+
+
+def fbp(calls: int = 3) -> None:
+    build.build()
+    ctx = fhr.Context(0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    N, Nr, K, Nv, Nc = 128, 64, 5, 90, 128
+    sino = torch.rand((Nv, Nc, Nr * K), device="cuda", generator=g)
+    for _ in range(calls):
+        ctx.fbp(sino, N)
+    torch.cuda.synchronize()
+    ctx.close()
+    print("ok")
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "nmf_pass"
     if case == "nmf_pass":
@@ -59,5 +104,9 @@ if __name__ == "__main__":
         nmf_pass(int(sys.argv[2]) if len(sys.argv) > 2 else 122880, Nk=1504, K=6, dtype=torch.bfloat16)
     elif case == "mbir":
         mbir()
+    elif case == "fmd":
+        fmd()
+    elif case == "fbp":
+        fbp()
     else:
         raise SystemExit("unknown case %r" % case)
