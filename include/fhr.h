@@ -342,7 +342,9 @@ fhr_status fhr_expand(fhr_ctx *ctx, int N, int Nr, int K, int Nk, int k0, int k1
  * Parameters: one FP32 array [W1 (H1 x Nk), b1 (H1), W2 (H2 x H1), b2 (H2),
  * W3 (K x H2), b3 (K)], weights row-major [out][in].  FP32 accumulation
  * throughout; with weights_bf16 the weights and the hidden activations are
- * rounded to bf16 (round to nearest even) before each contraction.
+ * rounded to bf16 (round to nearest even) before each contraction.  With bf16
+ * rows and bf16 weights (ldx, H1, H2 multiples of 8, X 16-byte aligned) the
+ * two wide layers run on the tensor cores.
  * Inputs X: [M][ldx] rows in x_dtype (FHR_F32 or FHR_BF16), e.g. rows of P.
  * ---------------------------------------------------------------------- */
 typedef struct fhr_mlp_dims_s {
@@ -354,7 +356,7 @@ typedef struct fhr_mlp_dims_s {
 
 /* Workspace for fhr_mlp_forward (train = 0) or fhr_mlp_grad (train = 1). */
 fhr_status fhr_mlp_workspace_size(fhr_ctx *ctx, const fhr_mlp_dims *dims, int train, size_t *bytes);
-/* Y [M][K] float = MLP(X) for any M (processed in chunks of 32768 rows). */
+/* Y [M][K] float = MLP(X) for any M (processed in chunks of 65536 rows). */
 fhr_status fhr_mlp_forward(fhr_ctx *ctx, const fhr_mlp_dims *dims, const float *params, int64_t M,
                            const void *X, float *Y, void *ws, size_t ws_bytes);
 /* Mean-squared error against T [M][K] (loss, a device double, may be NULL)
