@@ -131,10 +131,10 @@ def test_mbir_zero_channel(fx, orc):
 
 
 def test_channel_chunked_gathers_match_oracle(fx, orc):
-    # a sinogram slab over the gathers' L2 budget (180 x 256 rays x 192 values = 35 MB):
+    # a sinogram slab over the gathers' L2 budget (180 x 256 rays x 384 values = 71 MB):
     # the gathers run in channel chunks, chunk-major over the grid
     rng = np.random.default_rng(600)
-    N, Nc, Nv, Wl = 40, 256, 180, 192
+    N, Nc, Nv, Wl = 40, 256, 180, 384
     th = _angles(Nv)
     x = rng.uniform(size=(N, N, Wl)).astype(np.float32)
     y = fx.project(_dev(x), Nc, Nv).cpu().numpy()
@@ -145,11 +145,11 @@ def test_channel_chunked_gathers_match_oracle(fx, orc):
 
 
 def test_mbir_channel_chunked_matches_oracle(fx, orc):
-    # 180 x 96 rays x 512 values (35 MB): the MBIR gathers run in channel chunks.
+    # 180 x 96 rays x 1024 values (71 MB): the MBIR gathers run in channel chunks.
     # (The detector is kept about 1.5 N wide: sigma_x ~ mean / Nc, so a detector much
     # wider than the image makes the p = 1.2 prior nearly non-smooth and the iterates
     # sensitive to rounding at the 1e-3 level, a property of the problem, not the chunks.)
-    N, Nc, Nv, Nr, K = 64, 96, 180, 64, 8
+    N, Nc, Nv, Nr, K = 64, 96, 180, 128, 8
     V = _sino(orc, N, Nc, Nv, Nr, K, seed=9)
     sv, sx = orc.mbir_sigmas(V.astype(np.float64).reshape(-1, K), K, Nc)
     ref = orc.mbir(V.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, iters=3, momentum=True)
