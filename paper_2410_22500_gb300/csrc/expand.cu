@@ -24,41 +24,47 @@ __device__ __forceinline__ void st1<float>(float *dst, float a) { __stcs(dst, a)
 template <>
 __device__ __forceinline__ void st1<__nv_bfloat16>(__nv_bfloat16 *dst, float a) { *dst = __float2bfloat16_rn(a); }
 
+// One voxel per block row (threadIdx.y), its bins strided over threadIdx.x in
+// chunks of 4: the voxel's K coefficients are read once, the dictionary slab sits
+// transposed in shared memory ([K][nk rounded up to 4], float4 reads free of bank
+// conflicts), and each chunk is one 16-byte (f32) or 8-byte (bf16) streaming store.
 template <int K, typename TO, bool VEC>
 __global__ void __launch_bounds__(256) expand_kernel(const float *__restrict__ xs, const float *__restrict__ D,
                                                      int N, int Nr, int Nk, int k0, int nk, TO *__restrict__ xh) {
-    extern __shared__ float dsm[];   // [nk][K]
-    for (int i = threadIdx.x; i < nk * K; i += blockDim.x) dsm[i] = D[(size_t)k0 * K + i];
+    extern __shared__ __align__(16) float dsm[];   // [K][nk4]
+    const int nch = (nk + 3) / 4, nk4 = nch * 4;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    for (int i = tid; i < K * nk4; i += nt) {
+        const int j = i / nk4, k = i - j * nk4;
+        dsm[i] = k < nk ? D[(size_t)(k0 + k) * K + j] : 0.f;
+    }
     __syncthreads();
-    const int nch = (nk + 3) / 4;
-    const int64_t nvox = (int64_t)Nr * N * N;
-    const int64_t total = nvox * nch;
+    const int64_t NN = (int64_t)N * N, nvox = (int64_t)Nr * NN;
     const int Wl = Nr * K;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t vox = idx / nch;            // (r, iy, ix)
-        const int ch = (int)(idx - vox * nch);
-        const int64_t pix = vox % ((int64_t)N * N);
-        const int r = (int)(vox / ((int64_t)N * N));
+    for (int64_t vox = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; vox < nvox;
+         vox += (int64_t)gridDim.x * blockDim.y) {   // voxel (r, iy, ix)
+        const int r = (int)(vox / NN);
+        const int64_t pix = vox - r * NN;
         const float *a = xs + pix * Wl + r * K;
         float x[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) x[j] = __ldg(a + j);
-        const int kk = ch * 4;
-        float o[4];
+        TO *row = xh + vox * nk;
+        for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
+            const int kk = ch * 4;
+            float o[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            float s = 0.f;
-            if (kk + e < nk) {
-#pragma unroll
-                for (int j = 0; j < K; ++j) s = fmaf(x[j], dsm[(kk + e) * K + j], s);
+            for (int j = 0; j < K; ++j) {
+                const float4 d = *reinterpret_cast<const float4 *>(dsm + j * nk4 + kk);
+                o[0] = fmaf(x[j], d.x, o[0]);
+                o[1] = fmaf(x[j], d.y, o[1]);
+                o[2] = fmaf(x[j], d.z, o[2]);
+                o[3] = fmaf(x[j], d.w, o[3]);
             }
-            o[e] = s;
+            if (VEC) st4<TO>(row + kk, o[0], o[1], o[2], o[3]);
+            else
+                for (int e = 0; e < 4 && kk + e < nk; ++e) st1<TO>(row + kk + e, o[e]);
         }
-        TO *dst = xh + vox * nk + kk;
-        if (VEC) st4<TO>(dst, o[0], o[1], o[2], o[3]);
-        else
-            for (int e = 0; e < 4 && kk + e < nk; ++e) st1<TO>(dst + e, o[e]);
     }
 }
 
@@ -66,15 +72,22 @@ template <int K>
 static fhr_status launch_expand(fhr_ctx *ctx, const float *xs, const float *D, int N, int Nr, int Nk, int k0,
                                 int nk, int dt, void *xh) {
     const bool vec = (nk % 4 == 0) && aligned(xh, 16);
-    const size_t smem = sizeof(float) * (size_t)nk * K;
-    const int64_t total = (int64_t)Nr * N * N * ((nk + 3) / 4);
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(total, 256), (int64_t)ctx->sm_count * 8));
+    const int nch = (nk + 3) / 4;
+    const size_t smem = sizeof(float) * (size_t)nch * 4 * K;
+    // threads per voxel: whole warps, at most 8, covering the chunks in as few rounds as possible
+    const int warps = (nch + 31) / 32, rounds = (warps + 7) / 8;
+    const int bx = 32 * ((warps + rounds - 1) / rounds);
+    const int by = std::max(1, 256 / bx);
+    const int64_t nvox = (int64_t)Nr * N * N;
+    const int per_sm = std::max(1, std::min(2048 / (bx * by), (int)((size_t)ctx->max_smem_optin / std::max<size_t>(smem, 1))));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(nvox, by), (int64_t)ctx->sm_count * per_sm));
+    const dim3 block(bx, by);
 #define GO(T, V)                                                                                           \
     do {                                                                                                   \
         auto fn = expand_kernel<K, T, V>;                                                                  \
         FHR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));       \
-        FHR_TIMED(TM_EXPAND, (fn<<<blocks, 256, smem, ctx->stream>>>(xs, D, N, Nr, Nk, k0, nk,            \
-                                                                     reinterpret_cast<T *>(xh))));          \
+        FHR_TIMED(TM_EXPAND, (fn<<<blocks, block, smem, ctx->stream>>>(xs, D, N, Nr, Nk, k0, nk,          \
+                                                                       reinterpret_cast<T *>(xh))));        \
     } while (0)
     if (dt == FHR_F32) {
         if (vec) GO(float, true);
@@ -95,7 +108,7 @@ fhr_status expand_impl(fhr_ctx *ctx, int N, int Nr, int K, int Nk, int k0, int k
     FHR_ARG(dt == FHR_F32 || dt == FHR_BF16, "bad xh_dtype");
     if (k0 == 0 && k1 == 0) k1 = Nk;
     FHR_ARG(k0 >= 0 && k0 < k1 && k1 <= Nk, "bad bin slab [k0, k1)");
-    FHR_ARG((size_t)(k1 - k0) * K * sizeof(float) <= (size_t)ctx->max_smem_optin, "bin slab too large");
+    FHR_ARG((size_t)((k1 - k0 + 3) / 4 * 4) * K * sizeof(float) <= (size_t)ctx->max_smem_optin, "bin slab too large");
     FHR_CUDA(cudaSetDevice(ctx->device));
     const int nk = k1 - k0;
     switch (K) {
