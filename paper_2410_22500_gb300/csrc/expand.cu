@@ -68,6 +68,52 @@ __global__ void __launch_bounds__(256) expand_kernel(const float *__restrict__ x
     }
 }
 
+// The same with the dictionary in registers: a thread keeps the columns of its (at
+// most R) chunks for every voxel it visits, so the inner loop reads no shared memory
+// (with the slab in shared memory, the K x 4 floats read per 4-bin chunk outweighed
+// the chunk's own output write).  Slabs of up to R x 256 chunks (1024 R bins).
+template <int K, typename TO, bool VEC, int R>
+__global__ void __launch_bounds__(256) expand_reg_kernel(const float *__restrict__ xs, const float *__restrict__ D,
+                                                         int N, int Nr, int Nk, int k0, int nk,
+                                                         TO *__restrict__ xh) {
+    const int nch = (nk + 3) / 4;
+    float d[R][K][4];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int kk = (threadIdx.x + r * blockDim.x) * 4;
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) d[r][j][e] = kk + e < nk ? __ldg(D + (size_t)(k0 + kk + e) * K + j) : 0.f;
+    }
+    const int64_t NN = (int64_t)N * N, nvox = (int64_t)Nr * NN;
+    const int Wl = Nr * K;
+    for (int64_t vox = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; vox < nvox;
+         vox += (int64_t)gridDim.x * blockDim.y) {   // voxel (r, iy, ix)
+        const int rs = (int)(vox / NN);
+        const int64_t pix = vox - rs * NN;
+        const float *a = xs + pix * Wl + rs * K;
+        float x[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) x[j] = __ldg(a + j);
+        TO *row = xh + vox * nk;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int ch = threadIdx.x + r * blockDim.x;
+            if (ch >= nch) break;
+            const int kk = ch * 4;
+            float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) o[e] = fmaf(x[j], d[r][j][e], o[e]);
+            if (VEC) st4<TO>(row + kk, o[0], o[1], o[2], o[3]);
+            else
+                for (int e = 0; e < 4 && kk + e < nk; ++e) st1<TO>(row + kk + e, o[e]);
+        }
+    }
+}
+
 template <int K>
 static fhr_status launch_expand(fhr_ctx *ctx, const float *xs, const float *D, int N, int Nr, int Nk, int k0,
                                 int nk, int dt, void *xh) {
@@ -82,6 +128,20 @@ static fhr_status launch_expand(fhr_ctx *ctx, const float *xs, const float *D, i
     const int per_sm = std::max(1, std::min(2048 / (bx * by), (int)((size_t)ctx->max_smem_optin / std::max<size_t>(smem, 1))));
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(nvox, by), (int64_t)ctx->sm_count * per_sm));
     const dim3 block(bx, by);
+    if (rounds <= 2) {   // the dictionary columns fit in registers
+#define GOR(T, V)                                                                                          \
+    FHR_TIMED(TM_EXPAND, (expand_reg_kernel<K, T, V, 2><<<blocks, block, 0, ctx->stream>>>(                \
+                             xs, D, N, Nr, Nk, k0, nk, reinterpret_cast<T *>(xh))))
+        if (dt == FHR_F32) {
+            if (vec) GOR(float, true);
+            else GOR(float, false);
+        } else {
+            if (vec) GOR(__nv_bfloat16, true);
+            else GOR(__nv_bfloat16, false);
+        }
+#undef GOR
+        return FHR_OK;
+    }
 #define GO(T, V)                                                                                           \
     do {                                                                                                   \
         auto fn = expand_kernel<K, T, V>;                                                                  \
