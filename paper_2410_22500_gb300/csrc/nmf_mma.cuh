@@ -492,8 +492,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
 
     // ---------------- consumer warps
     const int c0 = warp * NKW;   // first bin of this warp
-    // D^T fragments, the 16 x k operand of phase 1: rows 0..7 the high parts
-    // (registers), rows 8..15 the low parts (shared memory), [k-step][a0/a1, a2/a3]
+    // D^T fragments, the 16 x k operand of phase 1: rows 0..7 the high parts,
+    // rows 8..15 the low parts, both in registers, [k-step][a0/a1, a2/a3]
     uint32_t da[KS][2];   // f32: big; bf16: hi
     // low parts in registers: bf16 as they are; f32 (TF32 remainders, below 2^-11 of
     // the value) rounded to bf16 and packed two to a register
