@@ -20,20 +20,29 @@ constexpr int kFmdInvSmem = 2304;   // subset inverses kept in shared memory (FP
 
 __global__ void fmd_region_partials(const float *__restrict__ xs, const uint8_t *__restrict__ lab, int64_t Nx, int Ns,
                                     int Nm, double *part, long long *cnt) {
-    const int t = threadIdx.x;   // (region i, channel j) = (t / Ns, t % Ns)
-    const int i = t / Ns, j = t % Ns;
+    // a lane per (region i, channel j) pair p, G warps covering the P pairs, and the
+    // block's voxel range split into R = 4 / G sub-ranges walked in voxel order; the
+    // sub-range sums are combined in order (deterministic)
+    __shared__ double ssum[4][kFmdMaxM * kFmdMaxS];
+    __shared__ long long scnt[4][kFmdMaxM * kFmdMaxS];
+    const int P = Nm * Ns, G = (P + 31) / 32, R = 4 / G;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = w / G, p = (w % G) * 32 + lane;
+    const int i = p / Ns, j = p % Ns;
     const int64_t per = (Nx + gridDim.x - 1) / gridDim.x;
     const int64_t lo = min(Nx, (int64_t)blockIdx.x * per), hi = min(Nx, lo + per);
+    const int64_t sub = (hi - lo + R - 1) / R;
     double s = 0.0;
     long long c = 0;
-    if (i < Nm) {
+    if (q < R && p < P) {
+        const int64_t a = min(hi, lo + q * sub), b = min(hi, a + sub);
         // eight voxels per step, their loads issued together; summed in voxel order
         constexpr int U = 8;
-        for (int64_t n0 = lo; n0 < hi; n0 += U) {
+        for (int64_t n0 = a; n0 < b; n0 += U) {
             int lb[U];
             float v[U];
 #pragma unroll
-            for (int k = 0; k < U; ++k) lb[k] = n0 + k < hi ? lab[n0 + k] : 0;
+            for (int k = 0; k < U; ++k) lb[k] = n0 + k < b ? lab[n0 + k] : 0;
 #pragma unroll
             for (int k = 0; k < U; ++k) v[k] = lb[k] == i + 1 ? xs[(n0 + k) * Ns + j] : 0.f;
 #pragma unroll
@@ -43,8 +52,20 @@ __global__ void fmd_region_partials(const float *__restrict__ xs, const uint8_t 
                     ++c;
                 }
         }
-        part[((size_t)blockIdx.x * Nm + i) * Ns + j] = s;
-        if (j == 0) cnt[(size_t)blockIdx.x * Nm + i] = c;
+        ssum[q][p] = s;
+        scnt[q][p] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x < P) {
+        const int pp = threadIdx.x;
+        double t = 0.0;
+        long long n = 0;
+        for (int r = 0; r < R; ++r) {
+            t += ssum[r][pp];
+            n += scnt[r][pp];
+        }
+        part[(size_t)blockIdx.x * P + pp] = t;
+        if (pp % Ns == 0) cnt[(size_t)blockIdx.x * Nm + pp / Ns] = n;
     }
 }
 
