@@ -7,7 +7,8 @@ precision); this module loads it with ctypes and adds the steps that use a
 library primitive (the SVD inside NNDSVD).
 
 Every function cites the passage of the paper it follows.  Parity status:
-  normalise        pinned (closed forms, planted offsets)
+  normalise        pinned (closed forms, planted offsets, per-bin and per-(pixel,
+                   bin) dead masks, hand-worked background with a dead entry)
   HALS / NMF       pinned (NNLS limits, monotone objective, exact recovery)
   NNDSVD           pinned (rank-1 exactness, sign invariance, hand example)
   projector        pinned (polygon clipping, adjointness, mass, disk chords)
