@@ -231,6 +231,16 @@ def splitmix64(seed, n):
     return out
 
 
+def kmpp_pick(d, u):
+    """The k-means++ pick: the first sample whose running sum of d exceeds u times the
+    total (the last sample with d > 0 if rounding leaves none); -1 for a zero total."""
+    L = lib()
+    L.or_kmpp_pick.restype = ctypes.c_long
+    L.or_kmpp_pick.argtypes = [_dp, ctypes.c_long, ctypes.c_double]
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    return int(L.or_kmpp_pick(_d(d), d.size, float(u)))
+
+
 def kmeans(P, S, K, iters, seed):
     """k-means of the sampled rows of P (the clustering start's first three steps).
     Returns (centres [K][Nk], labels [S], cost [iters+1], seeds [K])."""

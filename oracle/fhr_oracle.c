@@ -254,6 +254,24 @@ static double sqdist(const double *a, const double *b, int n)
     return s;
 }
 
+/* The k-means++ pick: the first sample whose running sum of d (squared distances
+ * to the nearest chosen centre) exceeds u times their total; when rounding leaves
+ * none, the last sample with d > 0.  -1 when the total is 0. */
+long or_kmpp_pick(const double *d, long S, double u)
+{
+    double tot = 0.0;
+    for (long i = 0; i < S; ++i) tot += d[i];
+    if (!(tot > 0.0)) return -1;
+    double target = u * tot, run = 0.0;
+    for (long i = 0; i < S; ++i) {
+        run += d[i];
+        if (run > target) return i;
+    }
+    for (long i = S - 1; i >= 0; --i)
+        if (d[i] > 0.0) return i;
+    return -1;
+}
+
 /* k-means on the sampled rows of P [Np][Nk].  C [K][Nk] receives the centres,
  * labels [S] (if non-NULL) the final assignment, cost [iters+1] (if non-NULL)
  * the sum of squared distances to the assigned centre before each centre
@@ -285,19 +303,8 @@ int or_kmeans(long Np, int Nk, const double *P, long S, int K, int iters, uint64
                 double e = sqdist(X + (size_t)i * Nk, C + (size_t)(m - 1) * Nk, Nk);
                 d[i] = (m == 1 || e < d[i]) ? e : d[i];
             }
-            double tot = 0.0;
-            for (long i = 0; i < S; ++i) tot += d[i];
-            if (tot > 0.0) {
-                double target = u * tot, run = 0.0;
-                pick = -1;
-                for (long i = 0; i < S; ++i) {
-                    run += d[i];
-                    if (run > target) { pick = i; break; }
-                }
-                if (pick < 0)  /* rounding: the last sample with d > 0 */
-                    for (long i = S - 1; i >= 0; --i)
-                        if (d[i] > 0.0) { pick = i; break; }
-            }
+            const long q = or_kmpp_pick(d, S, u);
+            if (q >= 0) pick = q;   /* all samples on chosen centres: keep the first-seed formula */
         }
         if (seeds) seeds[m] = pick;
         memcpy(C + (size_t)m * Nk, X + (size_t)pick * Nk, (size_t)Nk * sizeof(double));

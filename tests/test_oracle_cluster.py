@@ -101,3 +101,12 @@ def test_cluster_init_feeds_nmf():
     f0 = oracle.objective(P, D0, W0)
     _, _, obj = oracle.nmf(P, D0, W0, 20)
     assert obj[-1] < f0 and np.all(np.diff(obj) <= 1e-12 * f0)
+
+
+def test_kmeanspp_pick_takes_the_first_sample_exceeding_the_target(orc):
+    # running sums 1, 2, 4 against u * total: a sum equal to the target does not exceed it
+    assert orc.kmpp_pick([1.0, 1.0, 2.0], 0.25) == 1          # target 1: 1 is not > 1, 2 is
+    assert orc.kmpp_pick([1.0, 1.0, 2.0], 0.25 - 2.0 ** -54) == 0
+    assert orc.kmpp_pick([0.0, 0.0, 3.0, 0.0], 0.0) == 2       # zero-distance samples are never picked
+    assert orc.kmpp_pick([1.0, 2.0, 0.0, 0.0], 1.0 - 2.0 ** -53) == 1
+    assert orc.kmpp_pick([0.0, 0.0], 0.5) == -1                # every sample on a chosen centre

@@ -113,3 +113,12 @@ def test_noise_free_inverse_crime_recovery(orc):
     sv, sx = orc.mbir_sigmas(V.reshape(-1, 1), 1, Nc, snr_db=60.0)
     x = orc.mbir(V, N, 1, 1, th, sv, sx, iters=600, momentum=True)
     assert np.linalg.norm(x - xm) / np.linalg.norm(xm) < 0.02
+
+
+def test_sigma_reading_by_hand(orc):
+    # sigma_v = rms(V_j) 10^(-snr/20), sigma_x = 0.2 mean(V_j) / Nc, an all-zero channel 1:
+    # channel 0 = [3, 4]: rms^2 = 12.5, so sigma_v = sqrt(12.5e-3) at 30 dB, sigma_x = 0.2 * 3.5 / 10
+    V = np.array([[3.0, 0.0], [4.0, 0.0]])
+    sv, sx = orc.mbir_sigmas(V, 2, 10, snr_db=30.0)
+    np.testing.assert_allclose(sv, [np.sqrt(12.5e-3), 1.0], rtol=1e-14)
+    np.testing.assert_allclose(sx, [0.07, 1.0], rtol=1e-14)

@@ -184,3 +184,16 @@ def test_nndsvd_sign_invariant_and_nonnegative(orc):
     assert np.all(D1 >= 0) and np.all(W1 >= 0)
     # the first component carries the dominant rank-1 term exactly
     np.testing.assert_allclose(np.outer(W1[:, 0], D1[:, 0]), S[0] * np.outer(np.abs(U[:, 0]), np.abs(Vt[0])), atol=1e-12)
+
+
+def test_nndsvd_tie_goes_to_the_positive_pair(orc):
+    # column 1 has equal positive and negative products (|u+||v+| = |u-||v-|): the reading
+    # takes the positive pair, unit-normalised and scaled by sqrt(S_1 * product)
+    a, b = 0.6, 0.8
+    U = np.array([[1.0, a], [0.0, -a]])
+    Vt = np.array([[1.0, 0.0, 0.0], [b, -b, 0.0]])
+    S = np.array([4.0, 2.0])
+    D, W = orc.nndsvd_split(U, S, Vt, 2)
+    lam = np.sqrt(2.0 * a * b)
+    np.testing.assert_allclose(W[:, 1], [lam, 0.0], rtol=1e-15)
+    np.testing.assert_allclose(D[:, 1], [lam, 0.0, 0.0], rtol=1e-15)
