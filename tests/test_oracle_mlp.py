@@ -97,3 +97,11 @@ def test_training_reduces_loss(orc):
         loss, G = orc.mlp_grad(prm, X, T, dims)
         orc.adamw(prm, G, m, v, t, lr=3e-3, wd=0.0)
     assert loss < 0.2 * l0
+
+
+def test_softplus_follows_its_definition_up_to_the_threshold(orc):
+    # log(1 + e^z) itself (via e^-z, exact to rounding) for z up to 20, z beyond it
+    for z in (5.0, 10.5, 15.0, 19.9):
+        ref = z + math.log1p(math.exp(-z))
+        assert abs(orc.softplus(z) - ref) <= 2e-16 * ref
+    assert orc.softplus(20.5) == 20.5

@@ -197,3 +197,14 @@ def test_nndsvd_tie_goes_to_the_positive_pair(orc):
     lam = np.sqrt(2.0 * a * b)
     np.testing.assert_allclose(W[:, 1], [lam, 0.0], rtol=1e-15)
     np.testing.assert_allclose(D[:, 1], [lam, 0.0, 0.0], rtol=1e-15)
+
+
+def test_v_half_step_is_gauss_seidel_in_natural_order(orc):
+    # one pixel p = (1, 1), D = [[1, 0.5], [0.5, 1]], W = 0: r = D^T p = (1.5, 1.5),
+    # G = D^T D = [[1.25, 1], [1, 1.25]]; coordinate 0 first: w0 = 1.5 / 1.25 = 1.2,
+    # then w1 = (1.5 - 1 * 1.2) / 1.25 = 0.24 (the reverse order would give (0.24, 1.2))
+    P = np.array([[1.0, 1.0]])
+    D = np.array([[1.0, 0.5], [0.5, 1.0]])
+    W = np.zeros((1, 2))
+    orc.hals_update_W(P, D, W)
+    np.testing.assert_allclose(W[0], [1.2, 0.24], rtol=1e-15)
