@@ -21,6 +21,9 @@
  *     returned by fhr_workspace_status() after a stream synchronisation.
  *     No kernel of this library traps.
  *   - Sizes are element counts; strides are in elements.
+ *   - Every call makes the context's device current (cudaSetDevice) and
+ *     leaves it current on return; callers that use several devices from
+ *     one thread restore their own device afterwards.
  *
  * Notation (paper Sec. II): Nv views, Nr detector rows (= volume slices),
  * Nc detector columns, Nk wavelength bins, Np = Nv*Nr*Nc projections,
@@ -195,11 +198,19 @@ fhr_status fhr_decompose(fhr_ctx *ctx, const fhr_nmf_params *prm, const void *P,
  *   - All calls share the one array (it keeps the last call's contents; the
  *     call clears what must start at zero).  Calls that overlap on the GPU,
  *     from any stream or thread, race on it: serialise them.
- *   - Device-side status words are kept in the array and are not returned;
- *     a non-finite objective still shows up in obj.
+ *   - Errors found on the device (an expired bounded wait, a non-finite
+ *     objective) go to a status word kept in the array, which
+ *     fhr_decompose_static_status reads; check it after the call, since the
+ *     call itself returns before the device has run it.
  * Arguments as for fhr_decompose. */
 fhr_status fhr_decompose_static(fhr_ctx *ctx, const fhr_nmf_params *prm, const void *P,
                                 float *D, float *W, double *obj);
+/* Device status of the static calls on the context's device: synchronises
+ * the context's stream, returns FHR_OK or the first negative code that a
+ * static call since the last read reported, and clears it.  It covers every
+ * static call on the device (they share the one array), and allocates
+ * nothing.  FHR_OK before the first static call on the device. */
+fhr_status fhr_decompose_static_status(fhr_ctx *ctx);
 
 /* ------------------------------------------------------------------------
  * Parallel-beam projector of Eq. (porj_matd_rel)/(recon): the strip-area

@@ -60,3 +60,20 @@ extern "C" fhr_status fhr_decompose_static(fhr_ctx *ctx, const fhr_nmf_params *p
     ctx->prof_on = prof;
     return st;
 }
+
+// The status word at the start of the static array: bounded waits that
+// expired (FHR_ERR_TIMEOUT) and non-finite objectives (FHR_ERR_NONFINITE)
+// of the static calls land there, as they land in a caller workspace for
+// fhr_decompose.  Before the first static call on a device there is nothing
+// to report.
+extern "C" fhr_status fhr_decompose_static_status(fhr_ctx *ctx) {
+    if (!ctx) return FHR_ERR_ARG;
+    FHR_ARG(ctx->device >= 0 && ctx->device < kMaxDevices, "device ordinal out of range");
+    void *ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        ws = g_static_ptr[ctx->device];
+    }
+    if (!ws) return FHR_OK;
+    return fhr_workspace_status(ctx, ws);
+}

@@ -24,7 +24,7 @@ ENTRY_POINTS = (
     "fhr_normalise", "fhr_decompose_workspace_size", "fhr_decompose", "fhr_projector_workspace_size",
     "fhr_project", "fhr_backproject", "fhr_reconstruct_workspace_size", "fhr_reconstruct", "fhr_expand",
     "fhr_pipeline_workspace_size", "fhr_pipeline", "fhr_profile_enable", "fhr_profile_read",
-    "fhr_decompose_static", "fhr_mlp_workspace_size", "fhr_mlp_forward", "fhr_mlp_grad", "fhr_mlp_adamw",
+    "fhr_decompose_static", "fhr_decompose_static_status", "fhr_mlp_workspace_size", "fhr_mlp_forward", "fhr_mlp_grad", "fhr_mlp_adamw",
     "fhr_reconstruct_batch_workspace_size", "fhr_reconstruct_batch", "fhr_reconstruct_batch_autotune",
     "fhr_fbp_workspace_size", "fhr_fbp", "fhr_io_join", "fhr_fmd_workspace_size", "fhr_fmd",
 )
@@ -117,6 +117,7 @@ def load():
         L.fhr_pipeline_workspace_size.argtypes = [vp, ctypes.POINTER(PipelineParams), szp]
         L.fhr_pipeline.argtypes = [vp, ctypes.POINTER(PipelineParams), vp, vp, vp, vp, vp, vp, vp, vp, sz]
         L.fhr_decompose_static.argtypes = [vp, ctypes.POINTER(NmfParams), vp, vp, vp, vp]
+        L.fhr_decompose_static_status.argtypes = [vp]
         L.fhr_mlp_workspace_size.argtypes = [vp, ctypes.POINTER(MlpDims), ctypes.c_int, szp]
         L.fhr_mlp_forward.argtypes = [vp, ctypes.POINTER(MlpDims), vp, ctypes.c_int64, vp, vp, vp, sz]
         L.fhr_mlp_grad.argtypes = [vp, ctypes.POINTER(MlpDims), vp, ctypes.c_int64, vp, vp, vp, vp, vp, sz]

@@ -4,6 +4,7 @@ import math
 
 import numpy as np
 import pytest
+from _parity import assert_close, rel_l2 as _rel
 
 pytestmark = pytest.mark.gpu
 
@@ -12,10 +13,6 @@ def _dev(a):
     import torch
 
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
-
-
-def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def _angles(Nv):
@@ -54,10 +51,10 @@ def test_batch_matches_single_and_oracle(fx, orc, probs, momentum):
     V, got, _ = _run(fx, orc, probs, iters, momentum=momentum)
     for v, g, (N, Nc, Nv, Nr, K) in zip(V, got, probs):
         single = fx.reconstruct(_dev(v), N, Nr, K, iters, momentum=momentum).cpu().numpy()
-        assert _rel(g, single) <= 1e-6
+        assert_close(g, single, 1e-6)
         sv, sx = orc.mbir_sigmas(v.astype(np.float64).reshape(-1, K), K, Nc)
         ref = orc.mbir(v.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, iters=iters, momentum=momentum)
-        assert _rel(g, ref) <= 1e-4
+        assert_close(g, ref, 1e-4)
 
 
 def test_batch_explicit_sigmas_and_warm_start(fx, orc):
@@ -69,7 +66,7 @@ def test_batch_explicit_sigmas_and_warm_start(fx, orc):
         sv, sx = orc.mbir_sigmas(v.astype(np.float64).reshape(-1, K), K, Nc)
         ref = orc.mbir(v.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, p=1.5, iters=10,
                        x0=x.astype(np.float64))
-        assert _rel(g, ref) <= 1e-4
+        assert_close(g, ref, 1e-4)
 
 
 def test_tile_does_not_change_results(fx, orc):

@@ -2,6 +2,7 @@
 Lloyd iterations in FP64, D0 = centres, W0 = one HALS V step from zero)."""
 import numpy as np
 import pytest
+from _parity import assert_close, rel_l2 as _rel
 
 pytestmark = pytest.mark.gpu
 
@@ -10,10 +11,6 @@ def _dev(a):
     import torch
 
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
-
-
-def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def _padded(P, ldP):
@@ -45,8 +42,8 @@ def test_separated_clusters_match_oracle(fx, orc, Np, Nk, K, S):
     P32 = _blobs(rng, K, Np // K + 1, Nk)[:Np].astype(np.float32)
     D, W, _ = _gpu_start(fx, P32, K, S, 8, seed=3)
     Dr, Wr = orc.cluster_init(P32.astype(np.float64), K, S=S, iters=8, seed=3)
-    assert _rel(D, Dr) <= 1e-6
-    assert _rel(W, Wr) <= 1e-5
+    assert_close(D, Dr, 1e-6)
+    assert_close(W, Wr, 1e-5)
 
 
 def test_workload_start_and_iterates_match_oracle(fx, orc):
@@ -61,12 +58,12 @@ def test_workload_start_and_iterates_match_oracle(fx, orc):
     K = 3
     D, W, _ = _gpu_start(fx, P32, K, 1024, 20, seed=11)
     Dr, Wr = orc.cluster_init(P64, K, S=1024, iters=20, seed=11)
-    assert _rel(D, Dr) <= 1e-6
-    assert _rel(W, Wr) <= 1e-5
+    assert_close(D, Dr, 1e-6)
+    assert_close(W, Wr, 1e-5)
     D10, W10, obj = _gpu_start(fx, P32, K, 1024, 20, seed=11, nmf_iters=10)
     Dr10, Wr10, objr = orc.nmf(P64, Dr.astype(np.float32).astype(np.float64), Wr, 10)
-    assert _rel(D10, Dr10) <= 1e-4
-    assert _rel(W10, Wr10) <= 1e-4
+    assert_close(D10, Dr10, 1e-4)
+    assert_close(W10, Wr10, 1e-4)
     np.testing.assert_allclose(obj, objr, rtol=1e-4)
 
 
@@ -82,8 +79,8 @@ def test_bf16_input(fx, orc):
     Pr = Pb.float().numpy().astype(np.float64)
     D, W, _ = fx.decompose(Pb.cuda(), Nk, K, 0, init=fhr.INIT_CLUSTER, seed=5, kmeans_samples=600, kmeans_iters=5)
     Dr, Wr = orc.cluster_init(Pr, K, S=600, iters=5, seed=5)
-    assert _rel(D.cpu().numpy().astype(np.float64), Dr) <= 1e-6
-    assert _rel(W.cpu().numpy().astype(np.float64), Wr) <= 1e-5
+    assert_close(D.cpu().numpy().astype(np.float64), Dr, 1e-6)
+    assert_close(W.cpu().numpy().astype(np.float64), Wr, 1e-5)
 
 
 def test_default_sample_and_iterations(fx, orc):
@@ -92,7 +89,7 @@ def test_default_sample_and_iterations(fx, orc):
     P32 = _blobs(rng, 3, 400, 20)[:1000].astype(np.float32)
     D, _, _ = _gpu_start(fx, P32, 3, 0, 0, seed=1)
     Dr, _ = orc.cluster_init(P32.astype(np.float64), 3, S=1000, iters=20, seed=1)
-    assert _rel(D, Dr) <= 1e-6
+    assert_close(D, Dr, 1e-6)
 
 
 def test_rejects_bad_cluster_arguments(fx):

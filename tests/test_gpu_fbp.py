@@ -3,6 +3,7 @@ import math
 
 import numpy as np
 import pytest
+from _parity import assert_close, rel_l2 as _rel
 
 pytestmark = pytest.mark.gpu
 
@@ -13,10 +14,6 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
-
-
 @pytest.mark.parametrize("N,Nc,Nv,Wl", [(32, 48, 60, 3), (16, 23, 17, 8), (24, 40, 45, 12), (9, 13, 7, 1),
                                         (40, 64, 90, 33)])
 def test_fbp_matches_oracle(fx, orc, N, Nc, Nv, Wl):
@@ -25,7 +22,7 @@ def test_fbp_matches_oracle(fx, orc, N, Nc, Nv, Wl):
     th = np.arange(Nv) * (math.pi / Nv)
     got = fx.fbp(_dev(p), N).cpu().numpy()
     ref = orc.fbp(p.astype(np.float64), N, th)
-    assert _rel(got, ref) <= 1e-5
+    assert_close(got, ref, 1e-5)
 
 
 def test_fbp_of_disk_projections(fx, orc):
@@ -58,4 +55,4 @@ def test_pipeline_with_fbp_matches_oracle(fx, orc):
                      D, xh, obj=obj)
     assert fx.status(ws) == 0
     ref = orc.fhr_pipeline(y, y0, K, g.N, g.angles(), nmf_iters=iters, recon="fbp")
-    assert _rel(xh.cpu().numpy(), ref["xh"]) <= 1e-3
+    assert_close(xh.cpu().numpy(), ref["xh"], 1e-3)

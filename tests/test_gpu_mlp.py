@@ -4,6 +4,7 @@ import math
 
 import numpy as np
 import pytest
+from _parity import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -30,7 +31,7 @@ def test_forward_f32_matches_oracle(fx, orc, M, dims):
     d = fx.mlp_dims(*dims)
     Y = fx.mlp_forward(d, torch.from_numpy(prm.astype(np.float32)).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
     ref = orc.mlp_forward(prm, X.astype(np.float64), dims)
-    assert _rel(Y, ref) <= 1e-5
+    assert_close(Y, ref, 1e-5)
 
 
 def test_forward_bf16_weights_and_rows(fx, orc):
@@ -75,7 +76,7 @@ def test_forward_tensor_core_layers_at_the_volume_shape(fx, orc):
     X2[:, :1500] = X[:, :1500]
     d2 = fx.mlp_dims(*dims, ldx=1502, x_bf16=True, weights_bf16=True)
     Y2 = fx.mlp_forward(d2, p32, X2.cuda()).cpu().numpy()
-    assert _rel(Y, Y2) <= 2e-3
+    assert_close(Y, Y2, 2e-3)
 
 
 def test_gradient_bf16_rows_and_weights(fx, orc):
@@ -92,7 +93,7 @@ def test_gradient_bf16_rows_and_weights(fx, orc):
     loss, g = fx.mlp_grad(d, torch.from_numpy(prm.astype(np.float32)).cuda(), X.cuda(), torch.from_numpy(T).cuda())
     lref, gref = orc.mlp_grad(prm, X.float().numpy().astype(np.float64), T.astype(np.float64), dims)
     assert abs(float(loss.item()) - lref) <= 2e-2 * lref
-    assert _rel(g.cpu().numpy(), gref) <= 5e-2
+    assert_close(g.cpu().numpy(), gref, 5e-2)
 
 
 @pytest.mark.parametrize("M,dims", [(200, (30, 24, 12, 3)), (1500, (64, 48, 20, 5))])
@@ -109,12 +110,12 @@ def test_gradient_matches_oracle(fx, orc, M, dims):
     lref, gref = orc.mlp_grad(prm, X.astype(np.float64), T.astype(np.float64), dims)
     assert abs(float(loss.item()) - lref) <= 1e-5 * lref
     g = g.cpu().numpy()
-    assert _rel(g, gref) <= 1e-4
+    assert_close(g, gref, 1e-4)
     # every parameter block separately (a wrong layer hides in a global norm)
     Nk, H1, H2, K = dims
     o = 0
     for n in (H1 * Nk, H1, H2 * H1, H2, K * H2, K):
-        assert _rel(g[o:o + n], gref[o:o + n]) <= 1e-4
+        assert_close(g[o:o + n], gref[o:o + n], 1e-4)
         o += n
 
 
@@ -131,7 +132,7 @@ def test_adamw_matches_oracle(fx, orc):
         gr = rng.normal(size=n).astype(np.float32)
         fx.mlp_adamw(wt, torch.from_numpy(gr).cuda(), m, v, t, lr=1e-2, wd=0.01)
         orc.adamw(wr, gr.astype(np.float64), mr, vr, t, lr=1e-2, wd=0.01)
-    assert _rel(wt.cpu().numpy(), wr) <= 1e-6
+    assert_close(wt.cpu().numpy(), wr, 1e-6)
 
 
 def test_gpu_training_fits_a_teacher(fx, orc):

@@ -1,12 +1,9 @@
 """Algorithm 1 end to end on the GPU against the FP64 oracle."""
 import numpy as np
 import pytest
+from _parity import assert_close, rel_l2 as _rel
 
 pytestmark = pytest.mark.gpu
-
-
-def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def _run_gpu(fx, pb, K, nmf_iters, mbir_iters, host_io=False, **kw):
@@ -41,7 +38,7 @@ def test_tiny_2d_end_to_end(fx, orc):
     y, y0, D, xh, obj = _run_gpu(fx, pb, 3, 200, 30)
     ref = orc.fhr_pipeline(y, y0, 3, g.N, g.angles(), nmf_iters=200, mbir_iters=30)
     assert abs(obj[-1] - ref["obj"][-1]) <= 1e-3 * ref["obj"][-1]
-    assert _rel(xh, ref["xh"]) <= 1e-3
+    assert_close(xh, ref["xh"], 1e-3)
 
 
 def test_host_io_equals_device_io(fx):
@@ -74,7 +71,7 @@ def test_small_3d_end_to_end(fx, orc):
                      dead=dead)
     assert fx.status(ws) == 0
     ref = orc.fhr_pipeline(y, y0, 3, g.N, g.angles(), nmf_iters=100, mbir_iters=20, dead=pb.dead_bins)
-    assert _rel(xh.cpu().numpy(), ref["xh"]) <= 1e-3
+    assert_close(xh.cpu().numpy(), ref["xh"], 1e-3)
     assert np.all(D.cpu().numpy()[pb.dead_bins.astype(bool)] == 0)
 
 

@@ -3,6 +3,7 @@ import math
 
 import numpy as np
 import pytest
+from _parity import assert_close, rel_l2 as _rel
 
 pytestmark = pytest.mark.gpu
 
@@ -11,10 +12,6 @@ def _dev(a):
     import torch
 
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
-
-
-def _rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
 def _angles(Nv):
@@ -30,7 +27,7 @@ def test_forward_matches_oracle(fx, orc, N, Nc, Nv, Wl):
     x = rng.uniform(0, 1, size=(N, N, Wl)).astype(np.float32)
     y = fx.project(_dev(x), Nc, Nv).cpu().numpy()
     ref = orc.project(x.astype(np.float64), Nc, _angles(Nv))
-    assert _rel(y, ref) <= 1e-5
+    assert_close(y, ref, 1e-5)
 
 
 @pytest.mark.parametrize("N,Nc,Nv,Wl", GEOMS)
@@ -39,7 +36,7 @@ def test_backward_matches_oracle(fx, orc, N, Nc, Nv, Wl):
     e = rng.normal(size=(Nv, Nc, Wl)).astype(np.float32)
     x = fx.backproject(_dev(e), N).cpu().numpy()
     ref = orc.backproject(e.astype(np.float64), N, _angles(Nv))
-    assert _rel(x, ref) <= 1e-5
+    assert_close(x, ref, 1e-5)
 
 
 def test_adjointness_fp32(fx):
@@ -82,7 +79,7 @@ def test_custom_angles(fx, orc):
     th = np.sort(rng.uniform(0, math.pi, Nv))
     x = rng.uniform(size=(N, N, Wl)).astype(np.float32)
     y = fx.project(_dev(x), Nc, Nv, angles=torch.from_numpy(th).cuda()).cpu().numpy()
-    assert _rel(y, orc.project(x.astype(np.float64), Nc, th)) <= 1e-5
+    assert_close(y, orc.project(x.astype(np.float64), Nc, th), 1e-5)
 
 
 def _sino(orc, N, Nc, Nv, Nr, K, seed, noise=0.02):
@@ -102,10 +99,10 @@ def test_mbir_matches_oracle(fx, orc, N, Nc, Nv, Nr, K, momentum, p):
     iters = 20
     ref = orc.mbir(V.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, p=p, iters=iters, momentum=momentum)
     got = fx.reconstruct(_dev(V), N, Nr, K, iters, p=p, momentum=momentum).cpu().numpy()
-    assert _rel(got, ref) <= 1e-4
+    assert_close(got, ref, 1e-4)
     # explicit sigmas take the same path
     got2 = fx.reconstruct(_dev(V), N, Nr, K, iters, p=p, momentum=momentum, sigma_v=sv, sigma_x=sx).cpu().numpy()
-    assert _rel(got2, ref) <= 1e-4
+    assert_close(got2, ref, 1e-4)
 
 
 def test_mbir_no_prior_and_warm_start(fx, orc):
@@ -117,7 +114,7 @@ def test_mbir_no_prior_and_warm_start(fx, orc):
     ref = orc.mbir(V.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, beta=0.0, iters=15,
                    x0=x0.astype(np.float64))
     got = fx.reconstruct(_dev(V), N, Nr, K, 15, beta=0.0, sigma_v=sv, sigma_x=sx, xs=_dev(x0)).cpu().numpy()
-    assert _rel(got, ref) <= 1e-4
+    assert_close(got, ref, 1e-4)
 
 
 def test_mbir_zero_channel(fx, orc):
@@ -138,10 +135,10 @@ def test_channel_chunked_gathers_match_oracle(fx, orc):
     th = _angles(Nv)
     x = rng.uniform(size=(N, N, Wl)).astype(np.float32)
     y = fx.project(_dev(x), Nc, Nv).cpu().numpy()
-    assert _rel(y, orc.project(x.astype(np.float64), Nc, th)) <= 1e-5
+    assert_close(y, orc.project(x.astype(np.float64), Nc, th), 1e-5)
     e = rng.normal(size=(Nv, Nc, Wl)).astype(np.float32)
     xb = fx.backproject(_dev(e), N).cpu().numpy()
-    assert _rel(xb, orc.backproject(e.astype(np.float64), N, th)) <= 1e-5
+    assert_close(xb, orc.backproject(e.astype(np.float64), N, th), 1e-5)
 
 
 def test_mbir_channel_chunked_matches_oracle(fx, orc):
@@ -154,7 +151,7 @@ def test_mbir_channel_chunked_matches_oracle(fx, orc):
     sv, sx = orc.mbir_sigmas(V.astype(np.float64).reshape(-1, K), K, Nc)
     ref = orc.mbir(V.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, iters=3, momentum=True)
     got = fx.reconstruct(_dev(V), N, Nr, K, 3, momentum=True).cpu().numpy()
-    assert _rel(got, ref) <= 1e-4
+    assert_close(got, ref, 1e-4)
 
 
 def test_full_size_projector_pair_and_mbir(fx, orc):
@@ -167,15 +164,15 @@ def test_full_size_projector_pair_and_mbir(fx, orc):
     x = rng.uniform(0, 1, size=(N, N, Wl)).astype(np.float32)
     y = fx.project(_dev(x), Nc, Nv).cpu().numpy()
     ref = orc.project(x.astype(np.float64), Nc, _angles(Nv))
-    assert _rel(y, ref) <= 1e-5
+    assert_close(y, ref, 1e-5)
     e = rng.normal(size=(Nv, Nc, Wl)).astype(np.float32)
     xb = fx.backproject(_dev(e), N).cpu().numpy()
-    assert _rel(xb, orc.backproject(e.astype(np.float64), N, _angles(Nv))) <= 1e-5
+    assert_close(xb, orc.backproject(e.astype(np.float64), N, _angles(Nv)), 1e-5)
     V = ref.astype(np.float32)
     sv, sx = orc.mbir_sigmas(V.astype(np.float64).reshape(-1, K), K, Nc)
     got = fx.reconstruct(_dev(V), N, Nr, K, 2, momentum=True).cpu().numpy()
     want = orc.mbir(V.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, iters=2, momentum=True)
-    assert _rel(got, want) <= 1e-4
+    assert_close(got, want, 1e-4)
 
 
 @pytest.mark.parametrize("Wl", [4096, 4092, 1023, 2056])
@@ -186,10 +183,10 @@ def test_wide_channel_vectors(fx, orc, Wl):
     rng = np.random.default_rng(800 + Wl)
     x = rng.uniform(0, 1, size=(N, N, Wl)).astype(np.float32)
     y = fx.project(_dev(x), Nc, Nv).cpu().numpy()
-    assert _rel(y, orc.project(x.astype(np.float64), Nc, _angles(Nv))) <= 1e-5
+    assert_close(y, orc.project(x.astype(np.float64), Nc, _angles(Nv)), 1e-5)
     e = rng.normal(size=(Nv, Nc, Wl)).astype(np.float32)
     xb = fx.backproject(_dev(e), N).cpu().numpy()
-    assert _rel(xb, orc.backproject(e.astype(np.float64), N, _angles(Nv))) <= 1e-5
+    assert_close(xb, orc.backproject(e.astype(np.float64), N, _angles(Nv)), 1e-5)
 
 
 def test_too_wide_channel_vectors_are_rejected(fx):

@@ -122,3 +122,32 @@ def test_sigma_reading_by_hand(orc):
     sv, sx = orc.mbir_sigmas(V, 2, 10, snr_db=30.0)
     np.testing.assert_allclose(sv, [np.sqrt(12.5e-3), 1.0], rtol=1e-14)
     np.testing.assert_allclose(sx, [0.07, 1.0], rtol=1e-14)
+
+
+def test_momentum_point_clamp_by_hand(orc):
+    # The momentum point of the SQS iterations is z = max(0, x' + a (x' - x)) (reading of
+    # Eq. (recon) with positivity: the surrogate is built at a feasible point).  Worked by
+    # hand on a 2 x 2 image seen at 0 and pi/2 by two unit bins, so each ray sums one
+    # column or one row: A^T A 1 = 4 at every pixel, and with beta = 0 one step is
+    # x <- max(0, z + A^T (V - A z) / 4).  Data: columns (0.1, 2), rows (0.1, 2).
+    #   x1 = A^T V / 4             = [[0.05, 0.525], [0.525, 1.0]]      (a1 = 0, z1 = x1)
+    #   A z1: cols = rows = (0.575, 1.525); residual (-0.475, 0.475) on both
+    #   x2 = max(0, x1 + A^T r / 4) = [[0, 0.525], [0.525, 1.2375]]     (pixel (0,0): 0.05 - 0.2375 < 0)
+    #   a2 = (t1 - 1) / t2, t1 = (1 + sqrt 5) / 2, t2 = (1 + sqrt(1 + 4 t1^2)) / 2
+    #   z2 = max(0, x2 + a2 (x2 - x1)): pixel (0,0) gives max(0, -0.05 a2) = 0
+    #   A z2: cols = rows = (0.525, 1.7625 + 0.2375 a2); residual (-0.425, 0.2375 (1 - a2))
+    #   x3 = [[0, 0.525 + (0.2375 (1 - a2) - 0.425) / 4], [same, 1.35625 + 0.11875 a2]]
+    # Without the clamp z2[0,0] = -0.05 a2 and x3[0,1] would be larger by 0.0125 a2 (3.5e-3).
+    t1 = 0.5 * (1 + math.sqrt(5.0))
+    t2 = 0.5 * (1 + math.sqrt(1 + 4 * t1 * t1))
+    a2 = (t1 - 1) / t2
+    V = np.array([[0.1, 2.0], [0.1, 2.0]]).reshape(2, 2, 1)     # [view][bin][channel]
+    th = np.array([0.0, math.pi / 2])
+    one = np.array([1.0])
+    x2 = orc.mbir(V, 2, 1, 1, th, one, one, beta=0.0, iters=2, momentum=True)[:, :, 0]
+    np.testing.assert_allclose(x2, [[0.0, 0.525], [0.525, 1.2375]], atol=1e-12)
+    x3 = orc.mbir(V, 2, 1, 1, th, one, one, beta=0.0, iters=3, momentum=True)[:, :, 0]
+    off = 0.525 + (0.2375 * (1 - a2) - 0.425) / 4
+    want = np.array([[0.0, off], [off, 1.35625 + 0.11875 * a2]])
+    np.testing.assert_allclose(x3, want, atol=1e-12)
+    assert abs(0.0125 * a2) > 1e-3     # the unclamped point would miss this pin

@@ -44,6 +44,9 @@ def test_static_workspace_matches_caller_workspace(fx):
                                     ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(W.data_ptr()),
                                     ctypes.c_void_p(obj.data_ptr()))
         fx.check(rc)
+        # errors found on the device (an expired wait, a non-finite objective) are read
+        # from the static array's status word; this also synchronises the stream
+        assert L.fhr_decompose_static_status(fx._h) == fhr.OK, L.fhr_last_error(fx._h)
         torch.cuda.synchronize()
         assert _rel(D.cpu().numpy(), Dr) <= 1e-4, call
         assert _rel(W.cpu().numpy(), Wr) <= 1e-4, call
@@ -53,6 +56,7 @@ def test_static_workspace_matches_caller_workspace(fx):
     D, W = torch.empty_like(D0), torch.empty_like(W0)
     fx.check(L.fhr_decompose_static(fx._h, ctypes.byref(prm2), ctypes.c_void_p(P.data_ptr()),
                                     ctypes.c_void_p(D.data_ptr()), ctypes.c_void_p(W.data_ptr()), None))
+    assert L.fhr_decompose_static_status(fx._h) == fhr.OK, L.fhr_last_error(fx._h)
     Dn, Wn, _ = fx.decompose(P, Nk, K, 3, init=fhr.INIT_NNDSVD, seed=5, obj=False)
     torch.cuda.synchronize()
     assert _rel(D.cpu().numpy(), Dn.cpu().numpy()) <= 1e-4
