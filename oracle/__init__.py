@@ -49,7 +49,7 @@ def build(force: bool = False) -> str:
     """Compile fhr_oracle.c into liboracle.so beside it (gcc, -O2, no fast-math)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -66,6 +66,9 @@ def lib():
         if _lib is None:
             _lib = ctypes.CDLL(build())
             L = _lib
+            L.or_set_threads.restype = ctypes.c_int
+            L.or_set_threads.argtypes = [ctypes.c_int]
+            L.or_set_threads(1)
             L.or_normalise.restype = ctypes.c_int
             L.or_normalise.argtypes = [ctypes.c_int] * 4 + [_u16p, _u16p, _u8p, _u8p, ctypes.c_int, _dp, _dp]
             L.or_hals_update_W.argtypes = [ctypes.c_long, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
@@ -100,6 +103,12 @@ def lib():
             L.or_cluster_init.argtypes = [ctypes.c_long, ctypes.c_int, _dp, ctypes.c_long, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_uint64, _dp, _dp]
         return _lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's parallel loops (1 = serial, the default).
+    Results do not depend on it: every sum is taken in a fixed order."""
+    return int(lib().or_set_threads(int(n)))
 
 
 def _d(a):

@@ -7,8 +7,11 @@
  * smoke check and by the benchmark's CPU-baseline leg, and by nothing else.
  * It shares no code, header, table or constant with the CUDA library.
  *
- * Everything is double precision, single threaded, written as plain loops in
- * the order the paper states the steps.  Each function cites the passage it
+ * Everything is double precision, written as plain loops in the order the
+ * paper states the steps.  Loops whose iterations write disjoint outputs may
+ * run on several host threads (OpenMP); every sum is still taken in one fixed
+ * order, so each result is the same bit for bit whatever the thread count
+ * (or_set_threads).  Each function cites the passage it
  * follows.  Where the paper is silent, the reading taken is stated beside the
  * code (and listed with the design notes of the project).
  *
@@ -26,9 +29,25 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define OR_OK 0
 #define OR_ERR_ARG -1
 #define OR_ERR_NOMEM -2
+
+/* Host threads for the parallel loops (1 = serial); returns the count in use. */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 static double dmax(double a, double b) { return a > b ? a : b; }
 static double dmin(double a, double b) { return a < b ? a : b; }
@@ -61,6 +80,7 @@ int or_normalise(int Nv, int Nr, int Nc, int Nk,
     if (bg) {
         /* Appendix A: b_{v,k} = mean of -log(y/y0) over the background pixels whose
            entry is live; 0 when there is none */
+#pragma omp parallel for schedule(static)
         for (int v = 0; v < Nv; ++v)
             for (int k = 0; k < Nk; ++k) {
                 double s = 0.0;
@@ -76,6 +96,7 @@ int or_normalise(int Nv, int Nr, int Nc, int Nk,
                 b[(size_t)v * Nk + k] = n > 0 ? s / (double)n : 0.0;
             }
     }
+#pragma omp parallel for schedule(static)
     for (int v = 0; v < Nv; ++v)
         for (int r = 0; r < Nr; ++r)
             for (int c = 0; c < Nc; ++c) {
@@ -119,9 +140,11 @@ void or_gram(long rows, int K, const double *X, double *G)
 int or_hals_update_W(long Np, int Nk, int K, const double *P, const double *D, double *W)
 {
     if (K <= 0 || K > 64) return OR_ERR_ARG;
-    double G[64 * 64], r[64];
+    double G[64 * 64];
     or_gram(Nk, K, D, G);
+#pragma omp parallel for schedule(static)
     for (long j = 0; j < Np; ++j) {
+        double r[64];
         const double *p = P + j * Nk;
         double *w = W + j * K;
         for (int s = 0; s < K; ++s) {
@@ -147,11 +170,17 @@ int or_hals_update_D(long Np, int Nk, int K, const double *P, const double *W, d
     or_gram(Np, K, W, G);
     double *Q = (double *)calloc((size_t)Nk * K, sizeof(double));
     if (!Q) return OR_ERR_NOMEM;
-    for (long j = 0; j < Np; ++j)
-        for (int k = 0; k < Nk; ++k) {
-            double p = P[j * Nk + k];
-            for (int s = 0; s < K; ++s) Q[(size_t)k * K + s] += p * W[j * K + s];
-        }
+    /* Q = p^T V: each Q[k][s] is summed over j = 0..Np-1 in that order; a thread
+       takes a block of 16 bins at a time */
+#pragma omp parallel for schedule(dynamic)
+    for (int k0 = 0; k0 < Nk; k0 += 16) {
+        const int k1 = k0 + 16 < Nk ? k0 + 16 : Nk;
+        for (long j = 0; j < Np; ++j)
+            for (int k = k0; k < k1; ++k) {
+                double p = P[j * Nk + k];
+                for (int s = 0; s < K; ++s) Q[(size_t)k * K + s] += p * W[j * K + s];
+            }
+    }
     for (int k = 0; k < Nk; ++k) {
         double *d = D + (size_t)k * K;
         for (int s = 0; s < K; ++s) {
@@ -186,13 +215,23 @@ void or_normalise_columns(long Np, int Nk, int K, double *D, double *W, double *
 /* ||p - V D^T||_F^2, evaluated entry by entry (Eq. sub_extract_solve, no 1/2). */
 double or_objective(long Np, int Nk, int K, const double *P, const double *D, const double *W)
 {
-    double f = 0.0;
-    for (long j = 0; j < Np; ++j)
+    /* the squared residuals of each pixel row are summed over k, and the row sums
+       over j, each in ascending order */
+    double *row = (double *)malloc(sizeof(double) * (size_t)(Np > 0 ? Np : 1));
+    if (!row) return NAN;
+#pragma omp parallel for schedule(static)
+    for (long j = 0; j < Np; ++j) {
+        double fr = 0.0;
         for (int k = 0; k < Nk; ++k) {
             double e = P[j * Nk + k];
             for (int s = 0; s < K; ++s) e -= W[j * K + s] * D[(size_t)k * K + s];
-            f += e * e;
+            fr += e * e;
         }
+        row[j] = fr;
+    }
+    double f = 0.0;
+    for (long j = 0; j < Np; ++j) f += row[j];
+    free(row);
     return f;
 }
 
@@ -462,6 +501,7 @@ static void bin_range(double theta, double px, double py, int Nc, int *c0, int *
 void or_project(int N, int Nc, int Nv, const double *theta, int Wl, const double *x, double *y)
 {
     memset(y, 0, sizeof(double) * (size_t)Nv * Nc * Wl);
+#pragma omp parallel for schedule(dynamic)
     for (int v = 0; v < Nv; ++v)
         for (int iy = 0; iy < N; ++iy)
             for (int ix = 0; ix < N; ++ix) {
@@ -482,9 +522,11 @@ void or_project(int N, int Nc, int Nv, const double *theta, int Wl, const double
 void or_backproject(int N, int Nc, int Nv, const double *theta, int Wl, const double *y, double *x)
 {
     memset(x, 0, sizeof(double) * (size_t)N * N * Wl);
-    for (int v = 0; v < Nv; ++v)
-        for (int iy = 0; iy < N; ++iy)
-            for (int ix = 0; ix < N; ++ix) {
+    /* each pixel sums over views v, then bins c, in ascending order */
+#pragma omp parallel for schedule(dynamic)
+    for (int iy = 0; iy < N; ++iy)
+        for (int ix = 0; ix < N; ++ix)
+            for (int v = 0; v < Nv; ++v) {
                 double px = pix_x(ix, N), py = pix_x(iy, N);
                 int c0, c1;
                 bin_range(theta[v], px, py, Nc, &c0, &c1);
@@ -518,6 +560,7 @@ double or_ramp(int n)
 
 void or_ramp_filter(int Nv, int Nc, int Wl, const double *p, double *q)
 {
+#pragma omp parallel for schedule(static)
     for (int v = 0; v < Nv; ++v)
         for (int c = 0; c < Nc; ++c) {
             double *qo = q + ((size_t)v * Nc + c) * Wl;
@@ -650,6 +693,8 @@ static void sqs_step(int N, int Nr, int K, int Nc, int Nv, const double *theta, 
     double bw[10];
     int nnb;
     nb_weights(Nr, bw, &nnb);
+    /* every voxel's step reads z and bp only */
+#pragma omp parallel for schedule(static)
     for (int iy = 0; iy < N; ++iy)
         for (int ix = 0; ix < N; ++ix)
             for (int r = 0; r < Nr; ++r)
@@ -700,6 +745,7 @@ int or_mbir(int N, int Nr, int K, int Nc, int Nv, const double *theta, const dou
         if (prm->momentum) {
             double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
             double a = (t - 1.0) / tn;
+#pragma omp parallel for schedule(static)
             for (size_t i = 0; i < nx; ++i) {
                 double zn = xn[i] + a * (xn[i] - x[i]);
                 z[i] = dmax(zn, 0.0);
@@ -746,6 +792,7 @@ void or_mbir_sigmas(long rows, int K, const double *V, double snr_db, int Nc, do
  * ---------------------------------------------------------------------- */
 void or_expand(int N, int Nr, int K, int Nk, const double *xs, const double *D, double *xh)
 {
+#pragma omp parallel for schedule(static) collapse(2)
     for (int r = 0; r < Nr; ++r)
         for (int iy = 0; iy < N; ++iy)
             for (int ix = 0; ix < N; ++ix) {

@@ -70,5 +70,17 @@ def test_bench_algorithmic_pass_bytes():
     import bench
 
     # the 3-D workload: P (737,280 x 1200 f32) once, W (737,280 x 5 f32) read and written
-    assert bench.algorithmic_pass_bytes(737280, 1200, 5) == 737280 * 1200 * 4 + 2 * 737280 * 5 * 4 == 3568435200
+    assert bench.algorithmic_pass_bytes(737280, 1200, 4, 5) == 737280 * 1200 * 4 + 2 * 737280 * 5 * 4 == 3568435200
+    # the 256^3 precision form: P (7,864,320 x 1504 bf16) once, W (K = 6, f32) read and written
+    assert bench.algorithmic_pass_bytes(7864320, 1504, 2, 6) == 7864320 * 1504 * 2 + 2 * 7864320 * 6 * 4
     assert bench.whole_job_value(4, 10.0, 1000.0) == pytest.approx(40.0)
+
+
+def test_bench_cpu_info():
+    # the CPU baseline reports the cores it may use and the CPU model
+    import os
+
+    import bench
+
+    cores, model = bench.cpu_info()
+    assert cores == len(os.sched_getaffinity(0)) and model
