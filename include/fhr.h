@@ -297,6 +297,32 @@ fhr_status fhr_fmd(fhr_ctx *ctx, int64_t Nx, int Ns, int Nm, int Nk, const float
                    const float *D, float *T, float *xm, float *Dm, void *ws, size_t ws_bytes);
 
 /* ------------------------------------------------------------------------
+ * Signal-to-noise ratio of a reconstruction over regions of interest
+ * (Sec. V-B):
+ *   FHR_SNR_FHR, Eq. (snr_fhr): 10 log10( 1/(C Nm) sum_c sum_m (mu_{m,c} / sigma_c)^2 ),
+ *     x = x^h viewed as [Nx][Nk] (C = Nk): mu_{m,c} the mean of channel c over
+ *     the region inside material m, sigma_c its standard deviation over the
+ *     background region;
+ *   FHR_SNR_FMD, Eq. (snr_fmd): 10 log10( 1/Nm sum_m (mu_m / sigma_m)^2 ),
+ *     x = x^m [Nx][Nm] of fhr_fmd (C >= Nm): mu_m the mean of channel m over
+ *     the region inside material m, sigma_m its deviation over the background.
+ *   roi [Nx] u8: 0 = in no region, m + 1 = inside material m (m < Nm),
+ *   FHR_ROI_BACKGROUND = background.  The paper's regions are 20 x 20 pixel
+ *   squares; any voxel sets may be given.  sigma is the population standard
+ *   deviation (over the n background voxels, divided by n).
+ *   x, roi and snr_db (one double, in dB) are device pointers.  Nm <= 16,
+ *   Nx < 2^31.  An empty region or background sets FHR_ERR_ARG in the
+ *   workspace status word (snr_db = NaN); a zero deviation FHR_ERR_NONFINITE.
+ *   Sums are FP64, in a fixed order (deterministic).
+ * ---------------------------------------------------------------------- */
+#define FHR_SNR_FMD 0
+#define FHR_SNR_FHR 1
+#define FHR_ROI_BACKGROUND 255
+fhr_status fhr_snr_workspace_size(fhr_ctx *ctx, int64_t Nx, int C, int Nm, int mode, size_t *bytes);
+fhr_status fhr_snr(fhr_ctx *ctx, int64_t Nx, int C, int Nm, int mode, const float *x, const uint8_t *roi,
+                   double *snr_db, void *ws, size_t ws_bytes);
+
+/* ------------------------------------------------------------------------
  * Batched MBIR: Eq. (recon) for every channel and slice of nprob independent
  * problems of uneven size in ONE persistent cooperative launch (replayed from
  * a CUDA graph), two grid-wide phases per iteration (forward residual; fused

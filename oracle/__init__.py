@@ -19,6 +19,8 @@ Every function cites the passage of the paper it follows.  Parity status:
   FMD (semi-sup.)  pinned (hand-computed region means, exact recovery of a
                    nonnegative material mix, KKT on noisy data, App. B
                    identity D^m = D^s T^T recovering the material spectra)
+  SNR (Sec. V-B)   pinned (both equations worked by hand on a 7-voxel case,
+                   scale invariance, Gaussian noise of known sigma)
   FBP variant      pinned (textbook ramp samples, filter = direct convolution
                    with the kernel, disk reconstruction from analytic chords)
   clustering start pinned (published splitmix64 outputs, separated clusters
@@ -96,6 +98,7 @@ def lib():
             L.or_ramp_filter.argtypes = [ctypes.c_int] * 3 + [_dp, _dp]
             L.or_fbp.argtypes = [ctypes.c_int] * 3 + [_dp, ctypes.c_int, _dp, _dp]
             vp = ctypes.c_void_p
+            L.or_snr.argtypes = [ctypes.c_long, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _u8p, _dp]
             L.or_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_int, vp]
             L.or_splitmix64.restype = None
             L.or_kmeans.argtypes = [ctypes.c_long, ctypes.c_int, _dp, ctypes.c_long, ctypes.c_int, ctypes.c_int,
@@ -402,6 +405,25 @@ def expand(xs, D, N, Nr):
     xh = np.empty((Nr, N, N, Nk))
     lib().or_expand(N, Nr, K, Nk, _d(xs), _d(D), _d(xh))
     return xh
+
+
+# ---------------------------------------------------------------- SNR (Sec. V-B)
+SNR_FMD, SNR_FHR = 0, 1
+ROI_BACKGROUND = 255
+
+
+def snr(x, roi, Nm, mode):
+    """Eq. (snr_fmd) (mode SNR_FMD: channel m over region m) or Eq. (snr_fhr) (mode SNR_FHR:
+    every channel over every region), in dB.  x [Nx][C]; roi [Nx] u8: 0 none, m + 1 inside
+    material m, 255 background."""
+    x = _f64(x)
+    Nx, C = x.shape
+    roi = np.ascontiguousarray(roi, dtype=np.uint8).reshape(-1)
+    out = ctypes.c_double()
+    rc = lib().or_snr(Nx, C, Nm, mode, _d(x), roi.ctypes.data_as(_u8p), ctypes.byref(out))
+    if rc:
+        raise ValueError("or_snr failed: %d" % rc)
+    return out.value
 
 
 # ---------------------------------------------------------------- pipeline

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libfhr.so")
 F32, BF16 = 0, 1
 INIT_GIVEN, INIT_NNDSVD, INIT_LEARNED, INIT_CLUSTER = 0, 1, 2, 3
 RECON_MBIR, RECON_FBP = 0, 1
+SNR_FMD, SNR_FHR, ROI_BACKGROUND = 0, 1, 255
 OK, ERR_ARG, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 
 # Every entry point declared in include/fhr.h (checked by the ABI test).
@@ -27,6 +28,7 @@ ENTRY_POINTS = (
     "fhr_decompose_static", "fhr_decompose_static_status", "fhr_mlp_workspace_size", "fhr_mlp_forward", "fhr_mlp_grad", "fhr_mlp_adamw",
     "fhr_reconstruct_batch_workspace_size", "fhr_reconstruct_batch", "fhr_reconstruct_batch_autotune",
     "fhr_fbp_workspace_size", "fhr_fbp", "fhr_io_join", "fhr_fmd_workspace_size", "fhr_fmd",
+    "fhr_snr_workspace_size", "fhr_snr",
 )
 
 
@@ -129,6 +131,8 @@ def load():
         L.fhr_io_join.argtypes = [vp]
         L.fhr_fmd_workspace_size.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, szp]
         L.fhr_fmd.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int] + [vp] * 7 + [sz]
+        L.fhr_snr_workspace_size.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, szp]
+        L.fhr_snr.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, sz]
         L.fhr_fbp_workspace_size.argtypes = [vp, ctypes.POINTER(Geom), ctypes.c_int, szp]
         L.fhr_fbp.argtypes = [vp, ctypes.POINTER(Geom), ctypes.c_int, vp, vp, vp, sz]
         L.fhr_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -362,6 +366,24 @@ class Context:
         if check_status:
             self.check(self.status(ws))
         return T, xm, Dm
+
+    # ------------------------------------------------------------ SNR (Sec. V-B)
+    def snr(self, x, roi, Nm, mode, *, check_status=True):
+        """Eq. (snr_fmd) (mode SNR_FMD) or Eq. (snr_fhr) (mode SNR_FHR) in dB, as a device double.
+        x [Nx][C] f32 (any shape whose last axis is C), roi [Nx] u8 (0 none, m + 1 material m,
+        ROI_BACKGROUND background)."""
+        torch = _torch()
+        C = x.shape[-1]
+        x2 = x.reshape(-1, C)
+        Nx = x2.shape[0]
+        n = ctypes.c_size_t()
+        self.check(self.L.fhr_snr_workspace_size(self._h, Nx, C, Nm, mode, ctypes.byref(n)))
+        ws = self.workspace(n.value)
+        out = torch.empty(1, dtype=torch.float64, device=x.device)
+        self.check(self.L.fhr_snr(self._h, Nx, C, Nm, mode, _ptr(x2), _ptr(roi), _ptr(out), _ptr(ws), n.value))
+        if check_status:
+            self.check(self.status(ws))
+        return out
 
     # ------------------------------------------------------------ batched MBIR
     @staticmethod
