@@ -9,7 +9,7 @@
 // and optional momentum z <- max(0, x+ + a_t (x+ - x)).
 #include <math.h>
 
-#include "mbir.cuh"
+#include "proj_tma.cuh"
 
 namespace fhr {
 
@@ -143,6 +143,19 @@ static fhr_status launch_update_g(fhr_ctx *ctx, const fhr_geom *g, const GatherS
 
 static fhr_status launch_update(fhr_ctx *ctx, const fhr_geom *g, const MbirWs &w, const float *z, const float *xp,
                                 float *xn, float *zn, const MbirPrior &pr, float a, int K, int Wl) {
+    if (tma_gathers_ok(g, Wl)) {
+        TmaUpdate u;
+        u.z = z;
+        u.xprev = xp;
+        u.znext = zn;
+        u.dA = w.dA;
+        u.chp = w.chan;
+        u.pr = pr;
+        u.mom_a = a;
+        u.Nr = g->Nr;
+        u.K = K;
+        return tma_backward(ctx, g, w.t, Wl, w.e, xn, &u, w.status);
+    }
     const GatherShape s = gather_shape(Wl, gather_slab_values(g), kGatherMaxGBwd, kUpdateThreads);
     if (s.vw == 4 && s.g == 2) return launch_update_g<4, 2>(ctx, g, s, w, z, xp, xn, zn, pr, a, K, Wl);
     if (s.vw == 4) return launch_update_g<4, 1>(ctx, g, s, w, z, xp, xn, zn, pr, a, K, Wl);
@@ -208,7 +221,7 @@ fhr_status reconstruct_impl(fhr_ctx *ctx, const fhr_geom *g, const fhr_mbir_para
     else Z0 = X0;
     double tk = 1.0;
     for (int it = 0; it < p->iters; ++it) {
-        FHR_TRY(proj_forward(ctx, g, w.t, Wl, Z0, w.e, sino));
+        FHR_TRY(proj_forward(ctx, g, w.t, Wl, Z0, w.e, sino, w.status));
         float a = 0.f;
         if (p->momentum) {
             const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));

@@ -5,21 +5,22 @@
 //   producer warp   one 1-D bulk copy per pixel row into a padded shared
 //                   row (stride = 16 mod 128 bytes, so every fragment load
 //                   below is free of bank conflicts); tiles of 8 rows;
-//   13 consumer     each owns a fixed range of NKW bins (a multiple of 16):
-//   warps           phase 1 (tile t): partial r = D^T p for the 8 rows over
-//                   its bins with warp MMAs (D^T as the 16 x k operand: rows
+//   CW consumer     each owns a fixed range of NKW bins (a multiple of 16):
+//   warps (13 f32,  phase 1 (tile t): partial r = D^T p for the 8 rows over
+//   12 bf16)        its bins with warp MMAs (D^T as the 16 x k operand: rows
 //                   0..7 its high, rows 8..15 its low part; P^T as the k x 8
 //                   operand), written to shared memory; phase 3 (tile
 //                   t - LAG): Q += P^T w over its bins (P^T as the 16 x k
 //                   operand, w as the k x 8 operand), Q in MMA accumulators
 //                   for the whole launch;
-//   2 update warps  (alternate tiles) sum the 13 partials of r, run the HALS
-//                   V half-step of the 8 pixels and write W; they stage w
+//   15 - CW update  (tiles in turn) sum the CW partials of r, run the HALS
+//   warps           V half-step of the 8 pixels and write W; they stage w
 //                   for phase 3 and add w^T w to G_W from the staged
 //                   fragments with two MMAs (so the consumers' work is even).
-// The update warps and the producer sit on one SM sub-partition with a single
-// consumer warp (warps w and w + 4k share one), since the update is
-// latency-bound; with LAG = 2 its latency is off the per-tile critical path.
+// The update warps and the producer sit on one SM sub-partition (warps w and
+// w + 4k share one), with a single consumer warp when there are two update
+// warps and none when there are three, since the update is latency-bound;
+// with LAG = 2 its latency is off the per-tile critical path.
 //
 // Precision.  f32 P: TF32 products with the three-term split x = big + small
 // (big = x rounded or truncated to TF32, small = x - big) for P, D and w,
@@ -39,13 +40,21 @@ template <typename TP>
 struct MmaProducerLanes {
     static constexpr bool V = sizeof(TP) == 2;
 };
-constexpr int kMmaCW = 13;             // consumer warps (16 warps in all: 128 registers per thread)
-constexpr int kMmaThreads = (kMmaCW + 3) * 32;   // consumers, 2 update warps, producer
+// 16 warps in all (128 registers per thread): CW consumer warps, 15 - CW update
+// warps and the producer.  13 + 2 for f32 rows, 12 + 3 for bf16 (whose shorter
+// rows make the per-tile HALS update weigh more, and whose 1504-bin rows split
+// into 12 x 128 bins with less padding than 13 x 128)
+constexpr int kMmaWarps = 16;
+constexpr int kMmaThreads = kMmaWarps * 32;
+template <typename TP>
+struct MmaCW {
+    static constexpr int V = sizeof(TP) == 4 ? 13 : 12;
+};
 constexpr int kMmaWbStride = 48;       // bytes per s-row of the staged w (conflict-free ldmatrix)
 
 // bins per consumer warp (a multiple of 16)
-__host__ __device__ inline int mma_nkw(int ldP) {
-    const int per = (ldP + kMmaCW - 1) / kMmaCW;
+__host__ __device__ inline int mma_nkw(int ldP, int cw) {
+    const int per = (ldP + cw - 1) / cw;
     return (per + 15) / 16 * 16;
 }
 
@@ -55,7 +64,7 @@ struct MmaSmem {
 };
 
 // nb: hand-off buffers between phase 1 and phase 3 (pipeline lag + 1)
-__host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stages, int nb) {
+__host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stages, int nb, int cw) {
     MmaSmem L;
     size_t o = 0;
     auto take = [&](size_t bytes, size_t align) {
@@ -64,7 +73,7 @@ __host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stage
         o += bytes;
         return r;
     };
-    const size_t cols = (size_t)kMmaCW * mma_nkw(ldP);
+    const size_t cols = (size_t)cw * mma_nkw(ldP, cw);
     L.rs = (uint32_t)((cols * esize + 127) / 128 * 128 + 16);
     L.tiles = take((size_t)stages * kMmaRows * L.rs, 128);
     L.wst = take((size_t)stages * kMmaRows * kMaxK * sizeof(float), 128);   // W rows of each staged tile
@@ -73,8 +82,8 @@ __host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stage
     L.gsm = take((size_t)kMaxK * kMaxK * sizeof(float), 16);
     L.invd = take((size_t)kMaxK * sizeof(float), 16);
     L.wsc = take((size_t)kMaxK * sizeof(float), 16);
-    L.ssq = take((size_t)kMmaCW * sizeof(float), 16);
-    L.gwx = take((size_t)2 * 32 * 4 * sizeof(float), 16);    // G_W fragments of the two update warps
+    L.ssq = take((size_t)cw * sizeof(float), 16);
+    L.gwx = take((size_t)(kMmaWarps - 1 - cw) * 32 * 4 * sizeof(float), 16);   // G_W fragments of the update warps
     L.bars = take((size_t)(2 * stages + 2 * nb) * sizeof(uint64_t), 8);
     L.total = (o + 127) / 128 * 128;
     return L;
@@ -189,7 +198,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     constexpr int ES = (int)sizeof(TP);
     constexpr int KS = NKW / MmaK<TP>::STEP;    // GEMM1 k-steps per warp
     constexpr int MB = NKW / 16;                // GEMM2 m-blocks per warp
-    constexpr int NT = kMmaCW * 32;             // consumer threads
+    constexpr int CW = MmaCW<TP>::V;            // consumer warps
+    constexpr int NU = kMmaWarps - 1 - CW;      // update warps
+    constexpr int NT = CW * 32;                 // consumer threads
 
     const int tid = threadIdx.x;
     const int hw = tid >> 5, lane = tid & 31;   // hardware warp index
@@ -198,14 +209,17 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     // roles: warps 1 and 5 update, warp 9 produces (warps w and w + 4k share an SM
     // sub-partition, so the latency-bound update warps share theirs with one
     // consumer and the mostly idle producer); the other 13 warps are consumers 0..12
-    const int role = (hw == 1 || hw == 5) ? 1 : (hw == 9 ? 2 : 0);
-    const int warp = role == 0 ? hw - (hw > 1) - (hw > 5) - (hw > 9) : (role == 1 ? (hw == 5) : 0);
+    // (with three update warps, warp 13 is the third: sub-partition 1 then holds no consumer)
+    const bool upd3 = NU == 3 && hw == 13;
+    const int role = (hw == 1 || hw == 5 || upd3) ? 1 : (hw == 9 ? 2 : 0);
+    const int warp = role == 0 ? hw - (hw > 1) - (hw > 5) - (hw > 9) - (NU == 3 && hw > 13)
+                               : (role == 1 ? (hw == 1 ? 0 : (hw == 5 ? 1 : 2)) : 0);
     const int S = a.stages;
     const int64_t ntiles = (a.Np + kMmaRows - 1) / kMmaRows;
     const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const MmaSmem Lyt = mma_smem_layout(a.ldP, ES, S, NB);
+    const MmaSmem Lyt = mma_smem_layout(a.ldP, ES, S, NB, CW);
     const uint32_t sb = smem_u32(smem);
     const uint32_t tiles_a = sb + (uint32_t)Lyt.tiles;
     const uint32_t wb_a = sb + (uint32_t)Lyt.wb;
@@ -312,7 +326,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     if (role == 1) {
         // ---------------- update warps: warp u takes the tiles i with i % 2 == u;
         // lane = (row, group of 4 partial sums)
-        const int uw = warp;   // 0 or 1
+        const int uw = warp;   // 0 .. NU - 1
         const int row = lane >> 2, grp = lane & 3;
         const int lmat = lane >> 3;
         float gw[4] = {0.f, 0.f, 0.f, 0.f};   // G_W of this warp's tiles (rows s and s + 8 of the accumulator)
@@ -331,9 +345,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
             iv[s] = invd[s];
             sc[s] = wsc[s];
         }
-        int su = uw % S;
+        int su = uw % S;   // NU < S: the ring holds at least LAG + 2 stages
         uint32_t paru = 0;
-        for (int64_t i = uw; i < my_tiles; i += 2) {
+        for (int64_t i = uw; i < my_tiles; i += NU) {
             const int b = (int)(i % NB);
             const uint32_t hpar = (uint32_t)((i / NB) & 1);
             const int64_t r0 = (blockIdx.x + i * gridDim.x) * kMmaRows;
@@ -362,7 +376,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 report(a.status, FHR_ERR_TIMEOUT);
                 break;
             }
-            su += 2;
+            su += NU;
             if (su >= S) {
                 su -= S;
                 paru ^= 1u;
@@ -469,7 +483,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) gwx[(uw * 32 + lane) * 4 + e] = gw[e];
-        bar_sync(1, NT + 64);
+        bar_sync(1, NT + NU * 32);
         if (uw == 0) {
             // G_W[s][t]: accumulator rows s (high part) and s + 8 (low part), column t
             const int g = lane >> 2, tig = lane & 3;
@@ -478,13 +492,13 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                 const int t = 2 * tig + e;
                 float v = 0.f;
 #pragma unroll
-                for (int u = 0; u < 2; ++u) v += gwx[(u * 32 + lane) * 4 + e] + gwx[(u * 32 + lane) * 4 + 2 + e];
+                for (int u = 0; u < NU; ++u) v += gwx[(u * 32 + lane) * 4 + e] + gwx[(u * 32 + lane) * 4 + 2 + e];
                 if (g < K && t < K) a.Gpart[(size_t)blockIdx.x * K * K + g * K + t] = v;
             }
         }
         if (uw == 0 && lane == 0 && a.want_ssq) {
             float acc = 0.f;
-            for (int wp = 0; wp < kMmaCW; ++wp) acc += ssqs[wp];
+            for (int wp = 0; wp < CW; ++wp) acc += ssqs[wp];
             a.ssqpart[blockIdx.x] = acc;
         }
         return;
@@ -691,7 +705,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
     if (lane == 0) ssqs[warp] = ssq;
-    bar_sync(1, NT + 64);
+    bar_sync(1, NT + NU * 32);
 }
 
 }  // namespace fhr

@@ -1,6 +1,6 @@
 // Instantiations and launch configuration of the fused NMF pass: the
-// tensor-core kernel (nmf_mma.cuh) up to 1664 (f32) / 2288 (bf16) bins per
-// row (13 consumer warps x 128 / 176 bins), the CUDA-core kernel
+// tensor-core kernel (nmf_mma.cuh) up to 1664 (f32) / 2112 (bf16) bins per
+// row (13 consumer warps x 128 / 12 x 176 bins), the CUDA-core kernel
 // (nmf_pass.cuh) beyond.
 #include "nmf_internal.h"
 #include "nmf_mma.cuh"
@@ -70,12 +70,14 @@ static const void *pick_mma(int nkw) {
 
 static fhr_status mma_config(fhr_ctx *ctx, int K, int ldP, int p_dtype, PassConfig *cfg) {
     const int esize = p_dtype == FHR_BF16 ? 2 : 4;
-    const void *fn = p_dtype == FHR_BF16 ? pick_mma<__nv_bfloat16>(mma_nkw(ldP)) : pick_mma<float>(mma_nkw(ldP));
+    const int cw = p_dtype == FHR_BF16 ? MmaCW<__nv_bfloat16>::V : MmaCW<float>::V;
+    const void *fn = p_dtype == FHR_BF16 ? pick_mma<__nv_bfloat16>(mma_nkw(ldP, cw)) : pick_mma<float>(mma_nkw(ldP, cw));
     if (!fn) return FHR_ERR_UNSUPPORTED;
     const int nb = (p_dtype == FHR_BF16 ? MmaLag<__nv_bfloat16>::V : MmaLag<float>::V) + 1;
     int stages = 8;
-    while (stages > nb + 1 && mma_smem_layout(ldP, esize, stages, nb).total > (size_t)ctx->max_smem_optin) --stages;
-    const size_t smem = mma_smem_layout(ldP, esize, stages, nb).total;
+    while (stages > nb + 1 && mma_smem_layout(ldP, esize, stages, nb, cw).total > (size_t)ctx->max_smem_optin)
+        --stages;
+    const size_t smem = mma_smem_layout(ldP, esize, stages, nb, cw).total;
     if (smem > (size_t)ctx->max_smem_optin) return FHR_ERR_UNSUPPORTED;
     FHR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;

@@ -1,5 +1,5 @@
 // Projector tables, launches and the standalone projector entry points.
-#include "proj.cuh"
+#include "proj_tma.cuh"
 
 namespace fhr {
 
@@ -101,6 +101,9 @@ void proj_tables_carve(Carve &c, int N, int Nc, int Nv, ProjTables *t) {
     tt.fws = c.take<int>((size_t)Nv * Nc * N);
     tt.rowmaj = c.take<uint8_t>((size_t)Nv);
     tt.bk = c.take<float4>((size_t)Nv * N * N);
+    const int64_t NB = cdiv(Nc, kTmaRays), NTX = cdiv(N, kTmaTile);
+    tt.fspan = c.take<int>((size_t)Nv * NB * N);
+    tt.bspan = c.take<int>((size_t)Nv * NTX * NTX);
     if (t) *t = tt;
 }
 
@@ -119,6 +122,12 @@ fhr_status proj_build_tables(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &
     proj_table_fw<<<(unsigned)cdiv(nf, 256), 256, 0, ctx->stream>>>(g->angles, g->N, g->Nc, g->Nv, t);
     FHR_LAUNCHED();
     proj_table_bk<<<(unsigned)cdiv(nb, 256), 256, 0, ctx->stream>>>(g->angles, g->N, g->Nc, g->Nv, t);
+    FHR_LAUNCHED();
+    const int64_t ns = (int64_t)g->Nv * cdiv(g->Nc, kTmaRays) * g->N;
+    proj_span_fw<<<(unsigned)cdiv(ns, 256), 256, 0, ctx->stream>>>(t, g->N, g->Nc, g->Nv, t.fspan);
+    FHR_LAUNCHED();
+    const int64_t nt = (int64_t)g->Nv * cdiv(g->N, kTmaTile) * cdiv(g->N, kTmaTile);
+    proj_span_bk<<<(unsigned)cdiv(nt, 256), 256, 0, ctx->stream>>>(t, g->N, g->Nc, g->Nv, t.bspan);
     FHR_LAUNCHED();
     return FHR_OK;
 }
@@ -152,12 +161,15 @@ struct BwdLaunch {
 };
 
 fhr_status proj_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *x, float *y,
-                        const float *V) {
+                        const float *V, int *status) {
+    if (tma_gathers_ok(g, Wl)) return tma_forward(ctx, g, t, Wl, x, y, V, status);
     const GatherShape s = gather_shape(Wl, gather_slab_values(g), kGatherMaxGFwd);
     return gather_dispatch<FwdLaunch>(s, ctx, g, t, Wl, x, y, V);
 }
 
-fhr_status proj_backward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *y, float *x) {
+fhr_status proj_backward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *y, float *x,
+                         int *status) {
+    if (tma_gathers_ok(g, Wl)) return tma_backward(ctx, g, t, Wl, y, x, nullptr, status);
     const GatherShape s = gather_shape(Wl, gather_slab_values(g), kGatherMaxGBwd);
     return gather_dispatch<BwdLaunch>(s, ctx, g, t, Wl, y, x);
 }
@@ -198,7 +210,7 @@ extern "C" fhr_status fhr_project(fhr_ctx *ctx, const fhr_geom *g, int Wl, const
     if (!ctx) return FHR_ERR_ARG;
     ProjTables t;
     FHR_TRY(proj_common(ctx, g, Wl, x, y, ws, ws_bytes, &t));
-    return proj_forward(ctx, g, t, Wl, x, y, nullptr);
+    return proj_forward(ctx, g, t, Wl, x, y, nullptr, (int *)ws);
 }
 
 extern "C" fhr_status fhr_backproject(fhr_ctx *ctx, const fhr_geom *g, int Wl, const float *y, float *x, void *ws,
@@ -206,5 +218,5 @@ extern "C" fhr_status fhr_backproject(fhr_ctx *ctx, const fhr_geom *g, int Wl, c
     if (!ctx) return FHR_ERR_ARG;
     ProjTables t;
     FHR_TRY(proj_common(ctx, g, Wl, y, x, ws, ws_bytes, &t));
-    return proj_backward(ctx, g, t, Wl, y, x);
+    return proj_backward(ctx, g, t, Wl, y, x, (int *)ws);
 }

@@ -23,6 +23,8 @@ struct ProjTables {
     int *fws;          // [Nv][N][Nc] s0
     uint8_t *rowmaj;   // [Nv] 1: lines are image rows (|cos| >= |sin|)
     float4 *bk;        // [Nv][N*N] {w0, w1, w2, c0}
+    int *fspan;        // [Nv][ray blocks of 32][N] first pixel of the staged run (proj_tma.cuh)
+    int *bspan;        // [Nv][8 x 8 tiles] first bin of the staged slab
 };
 
 template <int VW>
@@ -271,9 +273,11 @@ static inline size_t gather_slab_values(const fhr_geom *g) {
 
 void proj_tables_carve(Carve &c, int N, int Nc, int Nv, ProjTables *t);
 fhr_status proj_build_tables(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t);
+// status: the device status word that the staged gathers report to (may be null)
 fhr_status proj_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *x, float *y,
-                        const float *V);
-fhr_status proj_backward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *y, float *x);
+                        const float *V, int *status = nullptr);
+fhr_status proj_backward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *y, float *x,
+                         int *status = nullptr);
 fhr_status check_geom(fhr_ctx *ctx, const fhr_geom *g, int Wl);
 
 }  // namespace fhr

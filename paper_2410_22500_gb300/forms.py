@@ -5,6 +5,8 @@ line per case; device timing with CUDA events on the library's stream).
     python -m paper_2410_22500_gb300.forms batched [n_problems] [iters]
     python -m paper_2410_22500_gb300.forms learned [n_train]
     python -m paper_2410_22500_gb300.forms fbp_fmd
+    python -m paper_2410_22500_gb300.forms dhr
+    python -m paper_2410_22500_gb300.forms ns_sweep
 
 `precision`: the 256^3 volume (6 ellipsoids, Nk = 1500, 120 views, 256 x 256
 detector, 100 counts per bin; P is 7.86M x 1500) through Algorithm 1 with P
@@ -35,6 +37,19 @@ plain form stopped at the iteration where it first came within 1e-3 of its own
 final objective, and the BF16 form from the NNDSVD start with the fewest
 iterations that reach the same target (what the learned start adds to BF16).
 
+`dhr`: the comparison of the paper's Table II on the 3-D workload's shapes (no dead
+bins): direct reconstruction of every wavelength bin by FBP (DHR; the bins in slabs
+of 64, each slab one fhr_fbp call on P's columns viewed as a sinogram) against FHR
+with FBP and FHR with MBIR; whole-path times and SNR_FHR (Eq. snr_fhr) of each x^h
+over the phantom's pure voxels (per material) and air at least 3 pixels from any
+material (background).  A timing reference for the per-bin path, not a product path.
+
+`ns_sweep`: the subspace-dimension experiment of Sec. V-D on a synthetic 3-material
+volume (128 x 128 x 32, Nk = 1200, 90 views, 200 counts/bin): for N_s = 1..8 (the
+fused pass takes K <= 8) the path (NNDSVD start, 200 NMF and 100 MBIR iterations)
+then semi-supervised FMD with the pure voxels as regions; the relative error of each
+estimated material spectrum against the phantom's, and SNR_FMD (Eq. snr_fmd) of x^m.
+
 `fbp_fmd`: the 3-D f32 workload (the benchmark's) through Algorithm 1 with the
 MBIR and with the FBP reconstruction (200 NMF iterations; 100 SQS iterations),
 whole-pipeline times and the FBP kernels' times; then the semi-supervised FMD
@@ -46,6 +61,7 @@ material spectrum D^m against the phantom's over the live bins.
 import ctypes
 import json
 import sys
+import time
 
 import numpy as np
 import torch
@@ -344,6 +360,124 @@ def fbp_fmd() -> None:
     ctx.close()
 
 
+def _rois(pb, margin=3):
+    """Region labels in voxel order (r, iy, ix): m + 1 on the pure voxels of material m,
+    background on air at least `margin` pixels (in-plane) from every material."""
+    from scipy import ndimage
+
+    g = pb.geom
+    frac = synth.volume_fractions(pb.phantom, g.N, g.Nr)             # [Nr][N][N][Nm]
+    lab = np.where(frac.max(axis=-1) >= 0.999, frac.argmax(axis=-1) + 1, 0).astype(np.uint8)
+    any_mat = frac.sum(axis=-1) > 0
+    near = ndimage.binary_dilation(any_mat, structure=np.ones((1, 2 * margin + 1, 2 * margin + 1), bool))
+    yy, xx = np.mgrid[0:g.N, 0:g.N] - 0.5 * (g.N - 1)
+    inside = (yy ** 2 + xx ** 2) < (0.5 * g.N - 2) ** 2
+    lab[(~near) & inside[None]] = fhr.ROI_BACKGROUND
+    return lab, frac
+
+
+def dhr() -> None:
+    build.build()
+    ctx = fhr.Context(0)
+    pb = synth.scaled(synth.volume_3d_f32, dead_frac=0.0)
+    g = pb.geom
+    K, Kb = 5, 64
+    y, y0 = synth.counts_torch(pb, device="cuda")
+    lab, frac = _rois(pb)
+    Nm = frac.shape[-1]
+    roi_r = torch.from_numpy(lab.reshape(-1)).cuda()                                   # (r, iy, ix)
+    roi_y = torch.from_numpy(np.ascontiguousarray(lab.transpose(1, 2, 0)).reshape(-1)).cuda()   # (iy, ix, r)
+    vb = g.Nr * g.N * g.N * pb.Nk
+    out = {"case": "dhr", "workload": "128x128x64 volume, Nk=1200, 90 views, 64x128 detector, 200 counts/bin, "
+                                      "5 materials, K=5 (FHR)",
+           "roi": {"materials": Nm, "signal_voxels": int(((lab > 0) & (lab < 255)).sum()),
+                   "background_voxels": int((lab == 255).sum())}}
+    # DHR: every bin reconstructed by FBP, in slabs of Kb bins
+    P = ctx.normalise(y, y0)
+    slabs = [(k0, min(pb.Nk, k0 + Kb)) for k0 in range(0, pb.Nk, Kb)]
+    xs_slab = torch.empty((g.N, g.N, g.Nr * Kb), dtype=torch.float32, device="cuda")
+    sino = torch.empty((g.Np, Kb), dtype=torch.float32, device="cuda")
+
+    def run_dhr(measure):
+        acc = []
+        for k0, k1 in slabs:
+            kb = k1 - k0
+            s_ = sino.view(-1)[:g.Np * kb].view(g.Np, kb)        # contiguous [Np][kb]
+            s_.copy_(P[:, k0:k1])
+            xs = ctx.fbp(s_.view(g.Nv, g.Nc, g.Nr * kb), g.N,
+                         xs=xs_slab.view(-1)[:g.N * g.N * g.Nr * kb].view(g.N, g.N, g.Nr * kb))
+            if measure:
+                db = float(ctx.snr(xs.view(-1, kb), roi_y, Nm, fhr.SNR_FHR).item())
+                acc.append((kb, 10 ** (db / 10)))
+        return acc
+
+    run_dhr(False)
+    t_dhr = _timed(ctx, lambda: run_dhr(False))
+    parts = run_dhr(True)
+    snr_dhr = 10 * np.log10(sum(kb * q for kb, q in parts) / sum(kb for kb, _ in parts))
+    out["dhr_fbp"] = {"ms": round(t_dhr, 2), "slabs": len(slabs), "voxel_bins_per_s": vb / (t_dhr / 1e3),
+                      "snr_fhr_db": round(float(snr_dhr), 3),
+                      "note": "normalised P given; per slab a column copy of P then fhr_fbp"}
+    del P, sino, xs_slab
+    torch.cuda.empty_cache()
+    D = torch.empty((pb.Nk, K), dtype=torch.float32, device="cuda")
+    xh = torch.empty((g.Nr, g.N, g.N, pb.Nk), dtype=torch.float32, device="cuda")
+    for name, recon in (("fhr_fbp", fhr.RECON_FBP), ("fhr_mbir", fhr.RECON_MBIR)):
+        prm = ctx.pipeline_params(Nv=g.Nv, Nr=g.Nr, Nc=g.Nc, Nk=pb.Nk, N=g.N, K=K, nmf_iters=NMF_ITERS,
+                                  mbir_iters=MBIR_ITERS, momentum=True, seed=17, recon=recon)
+        ws, wsb = ctx.pipeline_workspace(prm)
+        run = lambda: ctx.pipeline(prm, y, y0, D, xh, ws=ws, ws_bytes=wsb)
+        run()
+        ctx.check(ctx.status(ws))
+        ms = _timed(ctx, run)
+        ctx.check(ctx.status(ws))
+        db = float(ctx.snr(xh.view(-1, pb.Nk), roi_r, Nm, fhr.SNR_FHR).item())
+        out[name] = {"ms": round(ms, 2), "voxel_bins_per_s": vb / (ms / 1e3), "snr_fhr_db": round(db, 3),
+                     "note": "whole path from the counts (normalise, NNDSVD, 200 NMF iterations, reconstruction, "
+                             "expansion)"}
+        del ws
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def ns_sweep(max_ns: int = 8) -> None:
+    build.build()
+    ctx = fhr.Context(0)
+    pb = synth.make_problem(N=128, Nr=32, Nc=128, Nv=90, Nk=1200, Nm=3, I0=200, seed=3003)
+    g = pb.geom
+    y, y0 = synth.counts_torch(pb, device="cuda")
+    lab, frac = _rois(pb)
+    Nm = frac.shape[-1]
+    labels = torch.from_numpy(np.ascontiguousarray(np.where(lab == fhr.ROI_BACKGROUND, 0, lab).transpose(1, 2, 0))
+                              ).cuda()
+    roi = torch.from_numpy(np.ascontiguousarray(lab.transpose(1, 2, 0)).reshape(-1)).cuda()   # (iy, ix, r)
+    P = ctx.normalise(y, y0)
+    rows = []
+    for Ns in range(1, max_ns + 1):
+        t0 = time.perf_counter()
+        Ds, W, _ = ctx.decompose(P, pb.Nk, Ns, NMF_ITERS, init=fhr.INIT_NNDSVD, obj=False)
+        xs = ctx.reconstruct(W.view(g.Nv, g.Nc, g.Nr * Ns), g.N, g.Nr, Ns, MBIR_ITERS, momentum=True)
+        row = {"Ns": Ns}
+        if Ns >= Nm:
+            T, xm, Dm = ctx.fmd(xs, labels, Ds, Nm)
+            Dm_h = Dm.cpu().numpy().astype(np.float64)
+            err = [float(np.linalg.norm(Dm_h[:, m] - pb.spectra[:, m]) / np.linalg.norm(pb.spectra[:, m]))
+                   for m in range(Nm)]
+            row["Dm_rel_err"] = [round(e, 4) for e in err]
+            row["Dm_rel_err_mean"] = round(float(np.mean(err)), 4)
+            row["snr_fmd_db"] = round(float(ctx.snr(xm, roi, Nm, fhr.SNR_FMD).item()), 3)
+        else:
+            row["note"] = "Ns < Nm: FMD needs at least as many subspace channels as materials"
+        torch.cuda.synchronize()
+        row["s"] = round(time.perf_counter() - t0, 3)
+        rows.append(row)
+        del Ds, W, xs
+    print(json.dumps({"case": "ns_sweep", "workload": "128x128x32 volume, Nk=1200, 90 views, 128x32 detector, "
+                                                      "200 counts/bin, 3 materials", "rows": rows}), flush=True)
+    ctx.close()
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "precision"
     if case == "precision":
@@ -352,6 +486,10 @@ if __name__ == "__main__":
         fbp_fmd()
     elif case == "learned":
         learned(int(sys.argv[2]) if len(sys.argv) > 2 else 12)
+    elif case == "dhr":
+        dhr()
+    elif case == "ns_sweep":
+        ns_sweep()
     elif case == "batched":
         batched(int(sys.argv[2]) if len(sys.argv) > 2 else 40, int(sys.argv[3]) if len(sys.argv) > 3 else 100)
     else:

@@ -18,6 +18,9 @@ K = 6, the row length and K of the 256^3 precision form.
 64 slices x K = 5, 90 views x 128 bins; uniform random sinogram), four SQS
 iterations with momentum: launches of proj_fwd_kernel and mbir_update_kernel
 at the benchmark's shapes (profile with `-k regex:"proj_fwd|mbir_update" -s 2 -c 2`).
+`mbir_volume`: the same at the 256^3 precision form's shapes (N = 256, 256 slices x
+K = 6, 120 views x 256 bins: a 403 MB image and a 189 MB sinogram), three SQS
+iterations with momentum.
 `fmd`: the semi-supervised material decomposition of 1,048,576 voxels (the 3-D
 workload's volume), Ns = Nm = 5, seeded mixtures with 10% of the voxels labelled,
 Nk = 1200; three calls (fmd_region_partials, fmd_finish_T, fmd_gram, fmd_spectra,
@@ -48,12 +51,11 @@ def nmf_pass(Np: int = 92160, Nk: int = 1200, K: int = 5, iters: int = 3, dtype=
     print("ok")
 
 
-def mbir(iters: int = 4) -> None:
+def mbir(iters: int = 4, N: int = 128, Nr: int = 64, K: int = 5, Nv: int = 90, Nc: int = 128) -> None:
     build.build()
     ctx = fhr.Context(0)
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
-    N, Nr, K, Nv, Nc = 128, 64, 5, 90, 128
     sino = torch.rand((Nv, Nc, Nr * K), device="cuda", generator=g)
     ctx.reconstruct(sino, N, Nr, K, iters, momentum=True)
     torch.cuda.synchronize()
@@ -104,6 +106,8 @@ if __name__ == "__main__":
         nmf_pass(int(sys.argv[2]) if len(sys.argv) > 2 else 122880, Nk=1504, K=6, dtype=torch.bfloat16)
     elif case == "mbir":
         mbir()
+    elif case == "mbir_volume":
+        mbir(3, N=256, Nr=256, K=6, Nv=120, Nc=256)
     elif case == "fmd":
         fmd()
     elif case == "fbp":

@@ -18,6 +18,8 @@ def orc():
     import oracle
 
     oracle.lib()
+    # every oracle sum is taken in a fixed order, so the thread count changes only the time
+    oracle.set_threads(len(os.sched_getaffinity(0)))
     return oracle
 
 

@@ -62,8 +62,6 @@ def test_bf16_form_error_on_32_slices(fx, orc):
     # The GPU streams P as BF16 (normalised on the GPU from the counts); the oracle normalises
     # the same counts in FP64.  Both run 10 iterations from one seeded GIVEN start; the GPU's
     # factors are then evaluated against the FP64 P by the oracle.
-    import os
-
     import torch
 
     from paper_2410_22500_gb300 import fhr, synth
@@ -90,14 +88,10 @@ def test_bf16_form_error_on_32_slices(fx, orc):
     y0h = y0s.cpu().numpy().view(np.uint16)
     del ys, y0s
     torch.cuda.empty_cache()
-    orc.set_threads(len(os.sched_getaffinity(0)))
-    try:
-        P64 = orc.normalise(yh, y0h)
-        del yh
-        Do, Wo, objo = orc.nmf(P64, D0.astype(np.float64), W0.astype(np.float64), ITERS)
-        f_gpu = orc.objective(P64, Dg, Wg)
-    finally:
-        orc.set_threads(1)
+    P64 = orc.normalise(yh, y0h)
+    del yh
+    Do, Wo, objo = orc.nmf(P64, D0.astype(np.float64), W0.astype(np.float64), ITERS)
+    f_gpu = orc.objective(P64, Dg, Wg)
     num = den = 0.0
     for a in range(0, Np, 65536):
         ref = Wo[a:a + 65536] @ Do.T

@@ -195,3 +195,50 @@ def test_too_wide_channel_vectors_are_rejected(fx):
     for Wl in (4100, 1025):
         with pytest.raises(fhr.FhrError):
             fx.project(_dev(np.zeros((8, 8, Wl), np.float32)), 12, 6)
+
+
+# Shapes that take the shared-memory staged gathers (Nc and Wl multiples of 4): ragged ray
+# blocks (Nc not a multiple of 32), ragged 8 x 8 tiles (N not a multiple of 8), ragged channel
+# chunks (Wl not a multiple of 64), runs and slabs clipped to small images and detectors.
+TMA_GEOMS = [(61, 36, 50, 68), (256, 256, 120, 64), (5, 8, 9, 16), (13, 12, 33, 4), (100, 132, 77, 1540),
+             (57, 60, 45, 200)]
+
+
+@pytest.mark.parametrize("N,Nc,Nv,Wl", TMA_GEOMS)
+def test_staged_gathers_match_oracle(fx, orc, N, Nc, Nv, Wl):
+    rng = np.random.default_rng(900 + N + Wl)
+    th = _angles(Nv)
+    x = rng.uniform(0, 1, size=(N, N, Wl)).astype(np.float32)
+    y = fx.project(_dev(x), Nc, Nv).cpu().numpy()
+    assert_close(y, orc.project(x.astype(np.float64), Nc, th), 1e-5, what="forward")
+    e = rng.normal(size=(Nv, Nc, Wl)).astype(np.float32)
+    xb = fx.backproject(_dev(e), N).cpu().numpy()
+    assert_close(xb, orc.backproject(e.astype(np.float64), N, th), 1e-5, what="backward")
+
+
+def test_staged_gathers_custom_angles_and_adjoint(fx, orc):
+    import torch
+
+    rng = np.random.default_rng(950)
+    N, Nc, Nv, Wl = 70, 100, 23, 8
+    th = np.sort(rng.uniform(0, math.pi, Nv))
+    ang = torch.from_numpy(th).cuda()
+    x = rng.normal(size=(N, N, Wl)).astype(np.float32)
+    yv = rng.normal(size=(Nv, Nc, Wl)).astype(np.float32)
+    Ax = fx.project(_dev(x), Nc, Nv, angles=ang).cpu().numpy()
+    Aty = fx.backproject(_dev(yv), N, angles=ang).cpu().numpy()
+    assert_close(Ax, orc.project(x.astype(np.float64), Nc, th), 1e-5)
+    assert_close(Aty, orc.backproject(yv.astype(np.float64), N, th), 1e-5)
+    lhs = np.sum(Ax.astype(np.float64) * yv)
+    rhs = np.sum(x.astype(np.float64) * Aty)
+    assert abs(lhs - rhs) <= 1e-6 * np.sqrt(np.sum(Ax.astype(np.float64) ** 2) * np.sum(yv.astype(np.float64) ** 2))
+
+
+@pytest.mark.parametrize("N,Nc,Nv,Nr,K,momentum,p", [(61, 36, 50, 4, 3, True, 1.2), (40, 64, 90, 2, 2, False, 1.5),
+                                                     (29, 44, 31, 1, 8, True, 2.0)])
+def test_staged_mbir_matches_oracle(fx, orc, N, Nc, Nv, Nr, K, momentum, p):
+    V = _sino(orc, N, Nc, Nv, Nr, K, seed=N + 7 * Nr)
+    sv, sx = orc.mbir_sigmas(V.astype(np.float64).reshape(-1, K), K, Nc)
+    ref = orc.mbir(V.astype(np.float64), N, Nr, K, _angles(Nv), sv, sx, p=p, iters=12, momentum=momentum)
+    got = fx.reconstruct(_dev(V), N, Nr, K, 12, p=p, momentum=momentum).cpu().numpy()
+    assert_close(got, ref, 1e-4)

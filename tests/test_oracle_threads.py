@@ -29,10 +29,11 @@ def _run(orc, threads):
 
 
 def test_thread_count_does_not_change_results(orc):
+    prev = orc.set_threads(0)
     try:
         a = _run(orc, 1)
         b = _run(orc, 4)
     finally:
-        orc.set_threads(1)
+        orc.set_threads(prev)
     for u, v in zip(a, b):
         np.testing.assert_array_equal(u, v)
