@@ -102,7 +102,7 @@ fhr_status tma_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int
     FHR_CUDA(cudaFuncSetAttribute(proj_fwd_tma<kTmaFwdG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int NB = (int)cdiv(Nc, kTmaRays);
     const unsigned blocks = (unsigned)((int64_t)cdiv(Wl, kTmaCw) * Nv * NB);
-    FHR_TIMED(TM_PROJ_FWD, (proj_fwd_tma<kTmaFwdG><<<blocks, kTmaRays * kTmaCw / (4 * kTmaFwdG), smem, ctx->stream>>>(
+    FHR_TIMED(TM_PROJ_FWD, (proj_fwd_tma<kTmaFwdG><<<blocks, kTmaRays * kTmaCw / (4 * kTmaFwdG) + 32, smem, ctx->stream>>>(
                                mrow, mcol, mfw, mfws, t.fspan, t.rowmaj, y, V, N, Nc, Nv, Wl, span, status)));
     return FHR_OK;
 }
@@ -131,7 +131,7 @@ fhr_status tma_backward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, in
         FHR_CUDA(cudaFuncSetAttribute(proj_bwd_tma<kTmaUpdG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
         FHR_TIMED(TM_MBIR_UPDATE,
-                  (proj_bwd_tma<kTmaUpdG, true><<<blocks, kTmaTile * kTmaTile * kTmaCw / (4 * kTmaUpdG), smem,
+                  (proj_bwd_tma<kTmaUpdG, true><<<blocks, kTmaTile * kTmaTile * kTmaCw / (4 * kTmaUpdG) + 32, smem,
                                                   ctx->stream>>>(ms, mb, t.bspan, x, *upd, N, Nc, Nv, Wl, bins,
                                                                  status)));
     } else {
@@ -139,7 +139,7 @@ fhr_status tma_backward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, in
                                       (int)smem));
         TmaUpdate none{};
         FHR_TIMED(TM_PROJ_BWD,
-                  (proj_bwd_tma<kTmaBwdG, false><<<blocks, kTmaTile * kTmaTile * kTmaCw / (4 * kTmaBwdG), smem,
+                  (proj_bwd_tma<kTmaBwdG, false><<<blocks, kTmaTile * kTmaTile * kTmaCw / (4 * kTmaBwdG) + 32, smem,
                                                    ctx->stream>>>(ms, mb, t.bspan, x, none, N, Nc, Nv, Wl, bins,
                                                                   status)));
     }

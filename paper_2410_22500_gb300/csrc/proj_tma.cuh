@@ -4,7 +4,7 @@
 // The table-driven gathers of proj.cuh read every candidate value from L1/L2,
 // one dependent load per weight.  These kernels stage what a block needs next
 // in shared memory instead, several lines or views ahead, through a ring of
-// mbarrier-tracked tensor copies issued by one thread:
+// mbarrier-tracked tensor copies issued by a producer warp:
 //   forward   block = (view v, 32 consecutive rays, 64 channels).  Per image
 //             line l (the axis most parallel to the rays) the rays' candidate
 //             pixels lie in one run of at most 49 pixels; the run (box
@@ -31,12 +31,12 @@ namespace fhr {
 constexpr int kTmaRays = 32;        // rays per forward block
 constexpr int kTmaSpan = 56;        // pixels per staged line: >= ceil(31 sqrt 2) + 1 + 4
 constexpr int kTmaCw = 64;          // channels per block
-constexpr int kTmaFwdStages = 4;
+constexpr int kTmaFwdStages = 6;
 constexpr int kTmaTile = 8;         // backward tile side
 constexpr int kTmaBins = 16;        // bins per staged view: >= ceil(7 sqrt 2) + 1 + 3
-constexpr int kTmaBwdStages = 8;
+constexpr int kTmaBwdStages = 12;
 // channel groups of 4 per thread: forward, plain backward, backward + SQS update
-constexpr int kTmaFwdG = 1, kTmaBwdG = 1, kTmaUpdG = 2;
+constexpr int kTmaFwdG = 1, kTmaBwdG = 2, kTmaUpdG = 2;
 // largest image side and view count of the staged path (their run starts are kept in
 // shared memory)
 constexpr int kTmaMaxN = 4096, kTmaMaxNv = 8192;
@@ -51,11 +51,12 @@ constexpr uint32_t kTmaBwdStage = kTmaBwdS + kTmaTile * kTmaTile * 16;
 static_assert(kTmaFwdX % 128 == 0 && kTmaFwdStage % 128 == 0 && kTmaBwdS % 128 == 0 && kTmaBwdStage % 128 == 0,
               "stages keep 128-byte alignment");
 
+// stages, run starts, then the full and empty mbarriers
 __host__ __device__ inline size_t tma_fwd_smem(int N) {
-    return (size_t)kTmaFwdStages * kTmaFwdStage + (size_t)N * 4 + kTmaFwdStages * 8 + 16;
+    return (size_t)kTmaFwdStages * kTmaFwdStage + (size_t)N * 4 + kTmaFwdStages * 16 + 16;
 }
 __host__ __device__ inline size_t tma_bwd_smem(int Nv) {
-    return (size_t)kTmaBwdStages * kTmaBwdStage + (size_t)Nv * 4 + kTmaBwdStages * 8 + 16;
+    return (size_t)kTmaBwdStages * kTmaBwdStage + (size_t)Nv * 4 + kTmaBwdStages * 16 + 16;
 }
 
 // ---- tensor copies (PTX): global -> this CTA's shared memory, completion on an mbarrier
@@ -82,19 +83,23 @@ __device__ __forceinline__ void tma_drain(uint64_t *bars, int S, int from, int t
 
 // y[v][c][w] = sum over lines and candidates of A x (V non-null: y = V - A x).
 // Block = (channel chunk, view, ray block), chunk-major.  Threads: 32 rays x
-// TR, TR = 64 / (4 G); thread (r, t) holds channels w0 + 4 t + 4 TR g, g < G.
+// TR consumers, TR = 64 / (4 G) (thread (r, t) holds channels w0 + 4 t + 4 TR g,
+// g < G), then one producer warp whose lane 0 refills each stage as soon as
+// every consumer warp has released it (full / empty mbarriers, no block-wide
+// barrier inside the sweep).
 template <int G>
-__global__ void __launch_bounds__(kTmaRays * kTmaCw / (4 * G)) proj_fwd_tma(
+__global__ void __launch_bounds__(kTmaRays * kTmaCw / (4 * G) + 32) proj_fwd_tma(
     const __grid_constant__ CUtensorMap mx_row, const __grid_constant__ CUtensorMap mx_col,
     const __grid_constant__ CUtensorMap mfw, const __grid_constant__ CUtensorMap mfws, const int *__restrict__ fspan,
     const uint8_t *__restrict__ rowmaj, float *__restrict__ y, const float *__restrict__ V, int N, int Nc, int Nv,
     int Wl, int span_box, int *status) {
     constexpr int TR = kTmaCw / (4 * G);
-    constexpr int NT = kTmaRays * TR;
+    constexpr int NT = kTmaRays * TR;   // consumer threads
     constexpr int S = kTmaFwdStages;
     extern __shared__ __align__(128) unsigned char smem[];
     int *sstart = reinterpret_cast<int *>(smem + (size_t)S * kTmaFwdStage);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)S * kTmaFwdStage + (((size_t)N * 4 + 7) & ~(size_t)7));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * kTmaFwdStage + (((size_t)N * 4 + 7) & ~(size_t)7));
+    uint64_t *empty = full + S;
 
     const int NB = (Nc + kTmaRays - 1) / kTmaRays;
     int bid = blockIdx.x;
@@ -102,40 +107,57 @@ __global__ void __launch_bounds__(kTmaRays * kTmaCw / (4 * G)) proj_fwd_tma(
     bid -= chunk * Nv * NB;
     const int v = bid / NB, b = bid - v * NB;
     const int w0 = chunk * kTmaCw;
-    const bool rows = rowmaj[v] != 0;
     const int tid = threadIdx.x;
-    const int r = tid / TR, t = tid - r * TR;
-    const int c = b * kTmaRays + r;
-    const uint32_t tx = (uint32_t)kTmaCw * span_box * 4 + kTmaRays * 20;
 
-    for (int l = tid; l < N; l += NT) sstart[l] = fspan[((size_t)v * NB + b) * N + l];
+    for (int l = tid; l < N; l += NT + 32) sstart[l] = fspan[((size_t)v * NB + b) * N + l];
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NT / 32);
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    auto issue = [&](int l) {
-        const int st = l % S;
-        unsigned char *base = smem + (size_t)st * kTmaFwdStage;
-        mbar_arrive_expect_tx(&bars[st], tx);
-        if (rows) tma_load_3d(base, &mx_row, w0, sstart[l], l, &bars[st]);
-        else tma_load_3d(base, &mx_col, w0, l, sstart[l], &bars[st]);
-        tma_load_2d(base + kTmaFwdX, &mfw, b * kTmaRays * 4, v * N + l, &bars[st]);
-        tma_load_2d(base + kTmaFwdX + kTmaRays * 16, &mfws, b * kTmaRays, v * N + l, &bars[st]);
-    };
-    if (tid == 0)
-        for (int l = 0; l < min(S, N); ++l) issue(l);
 
+    if (tid >= NT) {
+        // ---- producer: lane 0 of the last warp
+        if (tid != NT) return;
+        const bool rows = rowmaj[v] != 0;
+        const uint32_t tx = (uint32_t)kTmaCw * span_box * 4 + kTmaRays * 20;
+        int l = 0;
+        for (; l < N; ++l) {
+            const int st = l % S;
+            if (l >= S && !mbar_wait_bounded(&empty[st], (uint32_t)((l / S - 1) & 1))) {
+                report(status, FHR_ERR_TIMEOUT);
+                break;
+            }
+            unsigned char *base = smem + (size_t)st * kTmaFwdStage;
+            mbar_arrive_expect_tx(&full[st], tx);
+            if (rows) tma_load_3d(base, &mx_row, w0, sstart[l], l, &full[st]);
+            else tma_load_3d(base, &mx_col, w0, l, sstart[l], &full[st]);
+            tma_load_2d(base + kTmaFwdX, &mfw, b * kTmaRays * 4, v * N + l, &full[st]);
+            tma_load_2d(base + kTmaFwdX + kTmaRays * 16, &mfws, b * kTmaRays, v * N + l, &full[st]);
+        }
+        tma_drain(full, S, l > S ? l - S : 0, l);   // no copy lands after this thread exits
+        return;
+    }
+
+    // ---- consumers
+    const int lane = tid & 31;
+    const int r = tid / TR, t = tid - r * TR;
+    const int c = b * kTmaRays + r;
+    const bool live = c < Nc;
     float4 acc[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const bool live = c < Nc;
-    int l = 0;
-    for (; l < N; ++l) {
+    for (int l = 0; l < N; ++l) {
         const int st = l % S;
         const unsigned char *base = smem + (size_t)st * kTmaFwdStage;
-        const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)((l / S) & 1));
-        if (ok && live) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], (uint32_t)((l / S) & 1)))) {
+            if (lane == 0) report(status, FHR_ERR_TIMEOUT);
+            return;   // the producer drains what it issued
+        }
+        if (live) {
             const float4 w = reinterpret_cast<const float4 *>(base + kTmaFwdX)[r];
             const int s = reinterpret_cast<const int *>(base + kTmaFwdX + kTmaRays * 16)[r] - sstart[l];
             if (s >= 0 && s <= span_box - 4) {
@@ -163,15 +185,8 @@ __global__ void __launch_bounds__(kTmaRays * kTmaCw / (4 * G)) proj_fwd_tma(
                 report(status, FHR_ERR_UNSUPPORTED);   // a run wider than the staged box
             }
         }
-        if (__syncthreads_or(!ok)) break;   // every thread leaves at the same line
-        if (tid == 0 && l + S < N) issue(l + S);
-    }
-    if (l < N) {
-        if (tid == 0) {
-            report(status, FHR_ERR_TIMEOUT);
-            tma_drain(bars, S, l, min(N, l + S));
-        }
-        return;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
     }
     if (!live) return;
 #pragma unroll
@@ -202,18 +217,20 @@ struct TmaUpdate {
 // Backward gather over 8 x 8 pixel tiles: x[pix][w] = sum over views and
 // candidate bins of A y (UPDATE: the SQS step from z, written to xout, with
 // the momentum point when u.znext is set).  Block = (channel chunk, tile),
-// chunk-major.  Threads: 64 pixels x TP, TP = 64 / (4 G).
+// chunk-major.  Threads: 64 pixels x TP consumers, TP = 64 / (4 G), then one
+// producer warp (full / empty mbarriers as in the forward gather).
 template <int G, bool UPDATE>
-__global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G), UPDATE ? 2 : 1) proj_bwd_tma(
+__global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G) + 32, UPDATE ? 2 : 1) proj_bwd_tma(
     const __grid_constant__ CUtensorMap msino, const __grid_constant__ CUtensorMap mbk, const int *__restrict__ bspan,
     float *__restrict__ xout, TmaUpdate u, int N, int Nc, int Nv, int Wl, int bins_box, int *status) {
     constexpr int TP = kTmaCw / (4 * G);
-    constexpr int NT = kTmaTile * kTmaTile * TP;
+    constexpr int NT = kTmaTile * kTmaTile * TP;   // consumer threads
     constexpr int S = kTmaBwdStages;
     extern __shared__ __align__(128) unsigned char smem[];
     int *bstart = reinterpret_cast<int *>(smem + (size_t)S * kTmaBwdStage);
-    uint64_t *bars =
+    uint64_t *full =
         reinterpret_cast<uint64_t *>(smem + (size_t)S * kTmaBwdStage + (((size_t)Nv * 4 + 7) & ~(size_t)7));
+    uint64_t *empty = full + S;
 
     const int NTX = (N + kTmaTile - 1) / kTmaTile;
     const int ntiles = NTX * NTX;
@@ -222,37 +239,54 @@ __global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G), UPDATE
     const int ty = tile / NTX, tx0 = tile - ty * NTX;
     const int w0 = chunk * kTmaCw;
     const int tid = threadIdx.x;
+
+    for (int vv = tid; vv < Nv; vv += NT + 32) bstart[vv] = bspan[(size_t)vv * ntiles + tile];
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NT / 32);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (tid >= NT) {
+        // ---- producer: lane 0 of the last warp
+        if (tid != NT) return;
+        const uint32_t txb = (uint32_t)kTmaCw * bins_box * 4 + kTmaTile * kTmaTile * 16;
+        int vv = 0;
+        for (; vv < Nv; ++vv) {
+            const int st = vv % S;
+            if (vv >= S && !mbar_wait_bounded(&empty[st], (uint32_t)((vv / S - 1) & 1))) {
+                report(status, FHR_ERR_TIMEOUT);
+                break;
+            }
+            unsigned char *base = smem + (size_t)st * kTmaBwdStage;
+            mbar_arrive_expect_tx(&full[st], txb);
+            tma_load_3d(base, &msino, w0, bstart[vv], vv, &full[st]);
+            tma_load_3d(base + kTmaBwdS, &mbk, tx0 * kTmaTile * 4, ty * kTmaTile, vv, &full[st]);
+        }
+        tma_drain(full, S, vv > S ? vv - S : 0, vv);   // no copy lands after this thread exits
+        return;
+    }
+
+    // ---- consumers
+    const int lane = tid & 31;
     const int p = tid / TP, t = tid - p * TP;
     const int py = p / kTmaTile, px = p - py * kTmaTile;
     const int iy = ty * kTmaTile + py, ix = tx0 * kTmaTile + px;
     const bool live = iy < N && ix < N;
-    const uint32_t txb = (uint32_t)kTmaCw * bins_box * 4 + kTmaTile * kTmaTile * 16;
-
-    for (int vv = tid; vv < Nv; vv += NT) bstart[vv] = bspan[(size_t)vv * ntiles + tile];
-    if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    auto issue = [&](int vv) {
-        const int st = vv % S;
-        unsigned char *base = smem + (size_t)st * kTmaBwdStage;
-        mbar_arrive_expect_tx(&bars[st], txb);
-        tma_load_3d(base, &msino, w0, bstart[vv], vv, &bars[st]);
-        tma_load_3d(base + kTmaBwdS, &mbk, tx0 * kTmaTile * 4, ty * kTmaTile, vv, &bars[st]);
-    };
-    if (tid == 0)
-        for (int vv = 0; vv < min(S, Nv); ++vv) issue(vv);
-
     float4 acc[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-    int vv = 0;
-    for (; vv < Nv; ++vv) {
+    for (int vv = 0; vv < Nv; ++vv) {
         const int st = vv % S;
         const unsigned char *base = smem + (size_t)st * kTmaBwdStage;
-        const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)((vv / S) & 1));
-        if (ok && live) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], (uint32_t)((vv / S) & 1)))) {
+            if (lane == 0) report(status, FHR_ERR_TIMEOUT);
+            return;   // the producer drains what it issued
+        }
+        if (live) {
             const float4 w = reinterpret_cast<const float4 *>(base + kTmaBwdS)[p];
             const int s = (int)w.w - bstart[vv];
             if (s >= 0 && s <= bins_box - 3) {
@@ -275,15 +309,8 @@ __global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G), UPDATE
                 report(status, FHR_ERR_UNSUPPORTED);   // a footprint wider than the staged slab
             }
         }
-        if (__syncthreads_or(!ok)) break;   // every thread leaves at the same view
-        if (tid == 0 && vv + S < Nv) issue(vv + S);
-    }
-    if (vv < Nv) {
-        if (tid == 0) {
-            report(status, FHR_ERR_TIMEOUT);
-            tma_drain(bars, S, vv, min(Nv, vv + S));
-        }
-        return;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
     }
     if (!live) return;
     const int pix = iy * N + ix;

@@ -25,9 +25,10 @@ per-problem times of the latter.
 `learned`: the learned warm start with BF16 P against the plain FP32 form.
 A 1500 -> 256 -> 128 -> 6 MLP (GELU, GELU, softplus; BF16 weights in the
 forward, FP32 accumulation) is trained by the library's kernels on the plain
-method's coefficients for n_train (default 12) seeded 128x128x32 phantoms
-(120 views, 128 x 32 detector, 50 counts/bin; 131072 sampled pixel rows each)
-whose six materials share one spectra library.  A held-out 256x256x128 volume
+method's coefficients (NNDSVD start, 100 iterations) for n_train (default
+2000) seeded 128x128x32 phantoms (120 views, 128 x 32 detector, 50
+counts/bin; 2048 sampled pixel rows each) whose six materials share one
+spectra library.  A held-out 256x256x128 volume
 (Nk = 1500, 120 views, 256 x 128 detector, 50 counts/bin) is then run through
 Algorithm 1 twice: the plain FP32 form (NNDSVD start, 200 iterations) and the
 learned + BF16 form with the fewest iterations whose factors reach the plain
@@ -183,7 +184,7 @@ def _first_within(obj, target):
     return int(hit[0]) + 1 if len(hit) else None
 
 
-def learned(n_train: int = 12) -> None:
+def learned(n_train: int = 2000, rows_per_phantom: int = 2048, target_iters: int = 100) -> None:
     from . import learned as lw
 
     build.build()
@@ -192,28 +193,32 @@ def learned(n_train: int = 12) -> None:
     Nk, K, H1, H2, iters = 1500, 6, 256, 128, 200
     lib = synth.spectra_library(Nk, K, seed=77)
     ldb = (Nk + 7) // 8 * 8
-    # training set: plain-method coefficients on the BF16 P of small phantoms
-    Xs, Ts = [], []
+    # training set: plain-method coefficients (NNDSVD start, target_iters iterations) on the
+    # BF16 P of n_train seeded 128x128x32 phantoms, rows_per_phantom pixel rows sampled from each
     gen = torch.Generator(device="cuda")
     gen.manual_seed(5)
+    X = torch.empty((n_train * rows_per_phantom, ldb), dtype=torch.bfloat16, device="cuda")
+    T = torch.empty((n_train * rows_per_phantom, K), dtype=torch.float32, device="cuda")
+    t_gen = time.perf_counter()
     for i in range(n_train):
         pb = synth.make_problem(N=128, Nr=32, Nc=128, Nv=120, Nk=Nk, Nm=K, I0=50, seed=5000 + i, spectra=lib,
-                                three_d=True)
+                                three_d=True, device="cuda")
         y, y0 = synth.counts_torch(pb, device="cuda")
         Pb = ctx.normalise(y, y0, p_dtype=fhr.BF16)
-        D, W, _ = ctx.decompose(Pb, Nk, K, iters, init=fhr.INIT_NNDSVD, obj=False)
+        D, W, _ = ctx.decompose(Pb, Nk, K, target_iters, init=fhr.INIT_NNDSVD, obj=False)
         perm = torch.as_tensor(lw.match_order(D.cpu().numpy(), lib), device="cuda")
-        idx = torch.randint(0, Pb.shape[0], (131072,), device="cuda", generator=gen)
-        Xs.append(Pb[idx].contiguous())
-        Ts.append(W[idx][:, perm].contiguous())
+        idx = torch.randint(0, Pb.shape[0], (rows_per_phantom,), device="cuda", generator=gen)
+        X[i * rows_per_phantom:(i + 1) * rows_per_phantom] = Pb[idx]
+        T[i * rows_per_phantom:(i + 1) * rows_per_phantom] = W[idx][:, perm]
         del y, y0, Pb, W
-    X, T = torch.cat(Xs), torch.cat(Ts)
-    del Xs, Ts
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
     dims = ctx.mlp_dims(Nk, H1, H2, K, ldx=ldb, x_bf16=True, weights_bf16=True)
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0[0].record(ctx.stream)
-    prm, hist = lw.train(ctx, dims, X, T, steps=3000, batch=4096, lr=2e-3, log_every=1000)
+    steps, batch = 6000, 8192
+    prm, hist = lw.train(ctx, dims, X, T, steps=steps, batch=batch, lr=2e-3, log_every=1000)
     t0[1].record(ctx.stream)
     torch.cuda.synchronize()
     train_ms = t0[0].elapsed_time(t0[1])
@@ -289,8 +294,8 @@ def learned(n_train: int = 12) -> None:
     vb = g.Nr * g.N * g.N * Nk
     print(json.dumps({
         "case": "learned", "workload": "256x256x128 volume, Nk=1500, 120 views, K=6, 50 counts/bin",
-        "train": {"phantoms": n_train, "rows": n_train * 131072, "steps": 3000, "batch": 4096, "ms": round(train_ms, 1),
-                  "loss": hist},
+        "train": {"phantoms": n_train, "rows": n_train * rows_per_phantom, "target_iters": target_iters,
+                  "set_s": round(t_gen, 1), "steps": steps, "batch": batch, "ms": round(train_ms, 1), "loss": hist},
         "plain_f32": {"iters": iters, "objective_fp32P": f_plain, "pipeline_ms": round(t_plain, 2),
                       "voxel_bins_per_s": vb / (t_plain / 1e3), "kernel_ms": k_plain},
         "plain_f32_own_tol": {"iters": n_plain_tol, "pipeline_ms": round(t_plain_tol, 2)},
@@ -301,7 +306,8 @@ def learned(n_train: int = 12) -> None:
                               "reached_plain_within_1e-3": bool(f_pb is not None and f_pb <= target),
                               "pipeline_ms": round(t_pb, 2)},
         "speedup_vs_plain_f32": round(t_plain / t_lb, 3),
-        "speedup_vs_plain_f32_own_tol": round(t_plain_tol / t_lb, 3)}), flush=True)
+        "speedup_vs_plain_f32_own_tol": round(t_plain_tol / t_lb, 3),
+        "speedup_vs_bf16_nndsvd": round(t_pb / t_lb, 3)}), flush=True)
     ctx.close()
 
 
@@ -485,7 +491,7 @@ if __name__ == "__main__":
     elif case == "fbp_fmd":
         fbp_fmd()
     elif case == "learned":
-        learned(int(sys.argv[2]) if len(sys.argv) > 2 else 12)
+        learned(int(sys.argv[2]) if len(sys.argv) > 2 else 2000)
     elif case == "dhr":
         dhr()
     elif case == "ns_sweep":

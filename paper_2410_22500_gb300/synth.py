@@ -211,6 +211,32 @@ def chords(ph: Phantom, g: Geometry, sub: int = 8) -> np.ndarray:
     return out
 
 
+def chords_torch(ph: Phantom, g: Geometry, device="cuda", sub: int = 8):
+    """chords() evaluated with torch on `device` (FP64, the same formula and bin
+    averaging), for drawing many phantoms quickly.  Returns [Nv][Nr][Nc][Nm]."""
+    import torch
+
+    f64 = torch.float64
+    th = torch.from_numpy(g.angles()).to(device, f64)
+    off = (torch.arange(sub, device=device, dtype=f64) + 0.5) / sub - 0.5
+    uc = (torch.arange(g.Nc, device=device, dtype=f64) - 0.5 * (g.Nc - 1))[:, None] + off[None, :]
+    out = torch.zeros((g.Nv, g.Nr, g.Nc, ph.Nm), dtype=f64, device=device)
+    cth, sth = torch.cos(th), torch.sin(th)
+    for r in range(g.Nr):
+        z = r - 0.5 * (g.Nr - 1)
+        for m, e in enumerate(slice_ellipses(ph, z)):
+            if e is None:
+                continue
+            cx, cy, A, B, phi = e
+            al = th - phi
+            s2 = ((A * torch.cos(al)) ** 2 + (B * torch.sin(al)) ** 2)[:, None, None]
+            up = uc[None] - (cx * cth + cy * sth)[:, None, None]
+            d = s2 - up * up
+            ch = torch.where(d > 0, 2.0 * A * B * torch.sqrt(torch.clamp(d, min=0)) / s2, torch.zeros_like(d))
+            out[:, r, :, m] = ch.mean(dim=2)
+    return out
+
+
 def volume_fractions(ph: Phantom, N: int, Nr: int, sub: int = 4) -> np.ndarray:
     """Ground-truth volume fractions x^m, [Nr][N][N][Nm], by sub x sub supersampling."""
     o = (np.arange(sub) + 0.5) / sub - 0.5
@@ -234,7 +260,8 @@ def volume_fractions(ph: Phantom, N: int, Nr: int, sub: int = 4) -> np.ndarray:
 
 def make_problem(*, N: int, Nr: int, Nc: int, Nv: int, Nk: int, Nm: int, I0: float,
                  seed: int, dead_frac: float = 0.0, peak_integral: float = 2.0,
-                 three_d: bool | None = None, spectra: np.ndarray | None = None) -> Problem:
+                 three_d: bool | None = None, spectra: np.ndarray | None = None,
+                 device: str | None = None) -> Problem:
     """Draw phantom, spectra and dead-bin mask; scale spectra so the largest
     noise-free line integral over all pixels and bins is about `peak_integral`.
     `spectra` [Nk][Nm] fixes the materials' spectral shapes (a shared library)."""
@@ -245,15 +272,23 @@ def make_problem(*, N: int, Nr: int, Nc: int, Nv: int, Nk: int, Nm: int, I0: flo
     ph = ellipsoid_phantom(rng, N, Nr, Nm) if three_d else disk_phantom(rng, N, Nm)
     lam = wavelengths(Nk)
     mu = material_spectra(rng, Nm, lam) if spectra is None else np.array(spectra, dtype=np.float64, copy=True)
-    C = chords(ph, g).reshape(-1, Nm)
-    bound = float((C * mu.max(axis=0)[None, :]).sum(axis=1).max())
+    if device is None:
+        C = chords(ph, g).reshape(-1, Nm)
+        bound = float((C * mu.max(axis=0)[None, :]).sum(axis=1).max())
+    else:   # the same bound from the chords drawn on `device`
+        import torch
+
+        Ct = chords_torch(ph, g, device).reshape(-1, Nm)
+        bound = float((Ct * torch.from_numpy(mu.max(axis=0)).to(Ct)[None, :]).sum(dim=1).max().item())
     mu *= peak_integral / max(bound, 1e-30)
     dead = np.zeros(Nk, dtype=np.uint8)
     if dead_frac > 0:
         nd = int(round(dead_frac * Nk))
         dead[rng.choice(Nk, size=nd, replace=False)] = 1
-    return Problem(geom=g, Nk=Nk, phantom=ph, spectra=mu, I0=float(I0),
-                   dead_bins=dead, seed=seed)
+    pb = Problem(geom=g, Nk=Nk, phantom=ph, spectra=mu, I0=float(I0), dead_bins=dead, seed=seed)
+    if device is not None:
+        pb.extra["device"] = device
+    return pb
 
 
 def noise_free_projection(pb: Problem) -> np.ndarray:
@@ -298,7 +333,10 @@ def counts_torch(pb: Problem, device="cuda", chunk_views: int = 8):
     g = pb.geom
     gen = torch.Generator(device=device)
     gen.manual_seed(pb.seed + 7919)
-    C = torch.from_numpy(chords(pb.phantom, g).reshape(g.Nv, g.Nr * g.Nc, -1)).to(device, torch.float32)
+    if pb.extra.get("device") is not None:   # drawn with chords_torch
+        C = chords_torch(pb.phantom, g, device).reshape(g.Nv, g.Nr * g.Nc, -1).to(torch.float32)
+    else:
+        C = torch.from_numpy(chords(pb.phantom, g).reshape(g.Nv, g.Nr * g.Nc, -1)).to(device, torch.float32)
     mu = torch.from_numpy(pb.spectra.T.copy()).to(device, torch.float32)   # [Nm][Nk]
     dead = torch.from_numpy(pb.dead_bins.astype(bool)).to(device)
     y = torch.empty((g.Nv, g.Nr, g.Nc, pb.Nk), dtype=torch.int16, device=device)

@@ -84,3 +84,15 @@ def test_bench_cpu_info():
 
     cores, model = bench.cpu_info()
     assert cores == len(os.sched_getaffinity(0)) and model
+
+
+def test_chords_torch_matches_numpy():
+    # the torch evaluation of the analytic chords (used to draw many phantoms) is the numpy one
+    from paper_2410_22500_gb300 import synth
+
+    pb = synth.make_problem(N=48, Nr=5, Nc=40, Nv=17, Nk=12, Nm=3, I0=50, seed=11, three_d=True)
+    a = synth.chords(pb.phantom, pb.geom)
+    b = synth.chords_torch(pb.phantom, pb.geom, "cpu").numpy()
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-12 * np.abs(a).max())
+    pb2 = synth.make_problem(N=48, Nr=5, Nc=40, Nv=17, Nk=12, Nm=3, I0=50, seed=11, three_d=True, device="cpu")
+    np.testing.assert_allclose(pb2.spectra, pb.spectra, rtol=1e-12)
