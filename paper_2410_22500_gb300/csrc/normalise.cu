@@ -5,10 +5,33 @@
 
 namespace fhr {
 
-// -log(y / y0) with counts clamped at 1: log of the correctly rounded ratio,
-// so the absolute error stays near one ulp of the result even when p is small.
-__device__ __forceinline__ float neglog_ratio(float y, float y0) {
-    return logf(__fdiv_rn(fmaxf(y0, 1.f), fmaxf(y, 1.f)));
+// -log(y / y0) = ln max(y0, 1) - ln max(y, 1).  Each logarithm is carried as
+// an FP32 pair hi + lo (hi = ln n rounded to FP32, lo the FP32 rounding of the
+// remainder), so p = (hi0 - hi) + (lo0 - lo) is within about one ulp of the
+// exact value even when p is small (hi0 - hi is exact when the two are within a
+// factor 2).  Counts below kLnTab read the pair from a per-block table in shared
+// memory (filled once per block in FP64), so the common case costs two table
+// reads and three additions; larger counts take an FP64 logarithm.
+constexpr int kLnTab = 2048;
+
+__device__ __forceinline__ float2 ln_pair(double n) {
+    const double d = log(n);
+    const float hi = (float)d;
+    return make_float2(hi, (float)(d - (double)hi));
+}
+
+__device__ __forceinline__ float2 ln_count(const float2 *tab, uint32_t n) {
+    return n < (uint32_t)kLnTab ? tab[n] : ln_pair((double)n);
+}
+
+__device__ __forceinline__ float neglog(const float2 *tab, uint32_t y, uint32_t y0) {
+    const float2 a = ln_count(tab, y0), b = ln_count(tab, y);
+    return (a.x - b.x) + (a.y - b.y);
+}
+
+__device__ __forceinline__ void fill_ln_table(float2 *tab) {
+    for (int i = threadIdx.x; i < kLnTab; i += blockDim.x) tab[i] = ln_pair((double)max(i, 1));
+    __syncthreads();
 }
 
 // dead entry (detector pixel (r, c), bin k): [Nk] or [Nr][Nc][Nk] mask
@@ -20,6 +43,8 @@ __device__ __forceinline__ bool is_dead(const uint8_t *dead, int per_pixel, int 
 // (0 when there is none); compensated sum.
 __global__ void offset_reduce_kernel(const uint16_t *y, const uint16_t *y0, const uint8_t *bg, const uint8_t *dead,
                                      int per_pixel, int Nv, int Nr, int Nc, int Nk, float *b) {
+    __shared__ float2 tab[kLnTab];
+    fill_ln_table(tab);
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y;
     if (k >= Nk) return;
@@ -29,9 +54,9 @@ __global__ void offset_reduce_kernel(const uint16_t *y, const uint16_t *y0, cons
         for (int c = 0; c < Nc; ++c) {
             if (!bg[r * Nc + c] || is_dead(dead, per_pixel, r, c, Nc, Nk, k)) continue;
             ++nb;
-            const float yy = y[(((size_t)v * Nr + r) * Nc + c) * Nk + k];
-            const float yo = y0[((size_t)r * Nc + c) * Nk + k];
-            const float x = neglog_ratio(yy, yo) - comp;
+            const uint32_t yy = y[(((size_t)v * Nr + r) * Nc + c) * Nk + k];
+            const uint32_t yo = y0[((size_t)r * Nc + c) * Nk + k];
+            const float x = neglog(tab, yy, yo) - comp;
             const float t = s + x;
             comp = (t - s) - x;
             s = t;
@@ -70,6 +95,8 @@ __global__ void __launch_bounds__(256) normalise_kernel(const uint16_t *__restri
                                                         const uint8_t *__restrict__ dead, int per_pixel,
                                                         const float *__restrict__ b, int Nv, int Nr, int Nc, int Nk,
                                                         int ldP, TO *__restrict__ P) {
+    __shared__ float2 tab[kLnTab];
+    fill_ln_table(tab);
     const int nch = (ldP + 7) / 8;
     const int64_t total = (int64_t)Nv * Nc * Nr * nch;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -90,14 +117,14 @@ __global__ void __launch_bounds__(256) normalise_kernel(const uint16_t *__restri
             const uint32_t aa[4] = {a.x, a.y, a.z, a.w}, oo[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                p[2 * i] = neglog_ratio((float)(aa[i] & 0xffffu), (float)(oo[i] & 0xffffu));
-                p[2 * i + 1] = neglog_ratio((float)(aa[i] >> 16), (float)(oo[i] >> 16));
+                p[2 * i] = neglog(tab, aa[i] & 0xffffu, oo[i] & 0xffffu);
+                p[2 * i + 1] = neglog(tab, aa[i] >> 16, oo[i] >> 16);
             }
         } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int k = k0 + i;
-                p[i] = k < Nk ? neglog_ratio((float)yr[k], (float)y0r[k]) : 0.f;
+                p[i] = k < Nk ? neglog(tab, yr[k], y0r[k]) : 0.f;
             }
         }
 #pragma unroll

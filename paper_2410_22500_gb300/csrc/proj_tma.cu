@@ -14,9 +14,12 @@ __global__ void proj_span_fw(const ProjTables t, int N, int Nc, int Nv, int *fsp
     const int b = (int)((idx / N) % NB);
     const int v = (int)(idx / ((int64_t)N * NB));
     const int *s0 = t.fws + ((size_t)v * N + l) * Nc;
-    int lo = s0[b * kTmaRays];
-    for (int c = b * kTmaRays + 1; c < min(Nc, (b + 1) * kTmaRays); ++c) lo = min(lo, s0[c]);
-    fspan[idx] = lo;
+    int lo = s0[b * kTmaRays], hi = lo;
+    for (int c = b * kTmaRays + 1; c < min(Nc, (b + 1) * kTmaRays); ++c) {
+        lo = min(lo, s0[c]);
+        hi = max(hi, s0[c]);
+    }
+    fspan[idx] = lo | ((hi + 4 - lo) << 16);   // first pixel of the run, run length
 }
 
 __global__ void proj_span_bk(const ProjTables t, int N, int Nc, int Nv, int *bspan) {
@@ -81,12 +84,11 @@ bool tma_gathers_ok(const fhr_geom *g, int Wl) {
 fhr_status tma_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *x, float *y,
                        const float *V, int *status) {
     const int N = g->N, Nc = g->Nc, Nv = g->Nv;
-    const int span = std::min(kTmaSpan, N);
     CUtensorMap mrow, mcol, mfw, mfws;
     {
         const uint64_t dims[3] = {(uint64_t)Wl, (uint64_t)N, (uint64_t)N};
         const uint64_t st[2] = {(uint64_t)Wl * 4, (uint64_t)N * Wl * 4};
-        const uint32_t brow[3] = {kTmaCw, (uint32_t)span, 1}, bcol[3] = {kTmaCw, 1, (uint32_t)span};
+        const uint32_t brow[3] = {kTmaCw, kTmaRunBox, 1}, bcol[3] = {kTmaCw, 1, kTmaRunBox};
         FHR_ARG(make_map(&mrow, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, x, dims, st, brow) &&
                     make_map(&mcol, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, x, dims, st, bcol),
                 "tensor map of the image could not be encoded");
@@ -103,7 +105,7 @@ fhr_status tma_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int
     const int NB = (int)cdiv(Nc, kTmaRays);
     const unsigned blocks = (unsigned)((int64_t)cdiv(Wl, kTmaCw) * Nv * NB);
     FHR_TIMED(TM_PROJ_FWD, (proj_fwd_tma<kTmaFwdG><<<blocks, kTmaRays * kTmaCw / (4 * kTmaFwdG) + 32, smem, ctx->stream>>>(
-                               mrow, mcol, mfw, mfws, t.fspan, t.rowmaj, y, V, N, Nc, Nv, Wl, span, status)));
+                               mrow, mcol, mfw, mfws, t.fspan, t.rowmaj, y, V, N, Nc, Nv, Wl, status)));
     return FHR_OK;
 }
 

