@@ -88,14 +88,23 @@ __global__ void __launch_bounds__(256) expand_reg_kernel(const float *__restrict
     }
     const int64_t NN = (int64_t)N * N, nvox = (int64_t)Nr * NN;
     const int Wl = Nr * K;
-    for (int64_t vox = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; vox < nvox;
-         vox += (int64_t)gridDim.x * blockDim.y) {   // voxel (r, iy, ix)
+    const int64_t vstep = (int64_t)gridDim.x * blockDim.y;
+    // the K coefficients of voxel (r, iy, ix); the next voxel's are loaded before
+    // this one's row is written, so their latency hides behind the stores
+    auto coef = [&](int64_t vox, float (&x)[K]) {
         const int rs = (int)(vox / NN);
-        const int64_t pix = vox - rs * NN;
-        const float *a = xs + pix * Wl + rs * K;
-        float x[K];
+        const float *a = xs + (vox - rs * NN) * Wl + rs * K;
 #pragma unroll
         for (int j = 0; j < K; ++j) x[j] = __ldg(a + j);
+    };
+    int64_t vox = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+    float xn[K];
+    if (vox < nvox) coef(vox, xn);
+    for (; vox < nvox; vox += vstep) {
+        float x[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) x[j] = xn[j];
+        if (vox + vstep < nvox) coef(vox + vstep, xn);
         TO *row = xh + vox * nk;
 #pragma unroll
         for (int r = 0; r < R; ++r) {

@@ -88,7 +88,11 @@ __device__ __forceinline__ void store1<float>(float *dst, float p) { *dst = p; }
 template <>
 __device__ __forceinline__ void store1<__nv_bfloat16>(__nv_bfloat16 *dst, float p) { *dst = __float2bfloat16_rn(p); }
 
-// One thread per (output pixel row j, chunk of 8 bins).  Output row j = (v*Nc + c)*Nr + r.
+// One warp per output pixel row j = (v*Nc + c)*Nr + r at a time (the row's
+// indices decomposed once), its lanes over chunks of 8 bins.  Consecutive warps
+// take the same detector pixel (r, c) in consecutive views, so each open-beam
+// row is read from HBM once and then from L2 (the open beam of a 256 x 256
+// detector with 1500 bins is 197 MB, more than L2).
 // VEC: counts rows are 16-byte aligned (Nk % 8 == 0), 8 counts per 16-byte load.
 template <bool VEC, typename TO>
 __global__ void __launch_bounds__(256) normalise_kernel(const uint16_t *__restrict__ y, const uint16_t *__restrict__ y0,
@@ -98,48 +102,52 @@ __global__ void __launch_bounds__(256) normalise_kernel(const uint16_t *__restri
     __shared__ float2 tab[kLnTab];
     fill_ln_table(tab);
     const int nch = (ldP + 7) / 8;
-    const int64_t total = (int64_t)Nv * Nc * Nr * nch;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = idx / nch;
-        const int ch = (int)(idx - j * nch);
-        const int r = (int)(j % Nr);
-        const int64_t vc = j / Nr;
-        const int c = (int)(vc % Nc);
-        const int v = (int)(vc / Nc);
+    const int lane = threadIdx.x & 31;
+    const int64_t rows = (int64_t)Nv * Nc * Nr;
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < rows; m += wstride) {
+        const int v = (int)(m % Nv);
+        const int64_t rc = m / Nv;
+        const int r = (int)(rc % Nr);
+        const int c = (int)(rc / Nr);
+        const int64_t j = ((int64_t)v * Nc + c) * Nr + r;
         const uint16_t *yr = y + (((size_t)v * Nr + r) * Nc + c) * Nk;
         const uint16_t *y0r = y0 + ((size_t)r * Nc + c) * Nk;
-        const int k0 = ch * 8;
-        float p[8];
-        if (VEC && k0 + 8 <= Nk) {
-            const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(yr + k0));
-            const uint4 o = __ldg(reinterpret_cast<const uint4 *>(y0r + k0));
-            const uint32_t aa[4] = {a.x, a.y, a.z, a.w}, oo[4] = {o.x, o.y, o.z, o.w};
+        const float *bv = b ? b + (size_t)v * Nk : nullptr;
+        TO *prow = P + (size_t)j * ldP;
+        for (int ch = lane; ch < nch; ch += 32) {
+            const int k0 = ch * 8;
+            float p[8];
+            if (VEC && k0 + 8 <= Nk) {
+                const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(yr + k0));
+                const uint4 o = __ldg(reinterpret_cast<const uint4 *>(y0r + k0));
+                const uint32_t aa[4] = {a.x, a.y, a.z, a.w}, oo[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                p[2 * i] = neglog(tab, aa[i] & 0xffffu, oo[i] & 0xffffu);
-                p[2 * i + 1] = neglog(tab, aa[i] >> 16, oo[i] >> 16);
+                for (int i = 0; i < 4; ++i) {
+                    p[2 * i] = neglog(tab, aa[i] & 0xffffu, oo[i] & 0xffffu);
+                    p[2 * i + 1] = neglog(tab, aa[i] >> 16, oo[i] >> 16);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int k = k0 + i;
+                    p[i] = k < Nk ? neglog(tab, yr[k], y0r[k]) : 0.f;
+                }
             }
-        } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int k = k0 + i;
-                p[i] = k < Nk ? neglog(tab, yr[k], y0r[k]) : 0.f;
+                float q = p[i];
+                if (bv && k < Nk) q -= bv[k];
+                q = fmaxf(q, 0.f);
+                if (k >= Nk || is_dead(dead, per_pixel, r, c, Nc, Nk, k)) q = 0.f;
+                p[i] = q;
             }
+            TO *dst = prow + k0;
+            if (k0 + 8 <= ldP) store8<TO>(dst, p);
+            else
+                for (int i = 0; i < 8 && k0 + i < ldP; ++i) store1<TO>(dst + i, p[i]);
         }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int k = k0 + i;
-            float q = p[i];
-            if (b && k < Nk) q -= b[(size_t)v * Nk + k];
-            q = fmaxf(q, 0.f);
-            if (k >= Nk || is_dead(dead, per_pixel, r, c, Nc, Nk, k)) q = 0.f;
-            p[i] = q;
-        }
-        TO *dst = P + (size_t)j * ldP + k0;
-        if (k0 + 8 <= ldP) store8<TO>(dst, p);
-        else
-            for (int i = 0; i < 8 && k0 + i < ldP; ++i) store1<TO>(dst + i, p[i]);
     }
 }
 
@@ -172,8 +180,8 @@ extern "C" fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *p, cons
     // the 8-bin chunks of the f32 output need ldP % 8 == 0 for full 32-byte stores;
     // other ldP take the scalar store tail
     const bool vec = (p->Nk % 8 == 0) && aligned(y, 16) && aligned(y0, 16);
-    const int64_t total = (int64_t)p->Nv * p->Nc * p->Nr * (p->ldP / 8 + (p->ldP % 8 ? 1 : 0));
-    const int blocks = (int)std::min<int64_t>(cdiv(total, 256), (int64_t)ctx->sm_count * 16);
+    const int64_t rows = (int64_t)p->Nv * p->Nc * p->Nr;
+    const int blocks = (int)std::min<int64_t>(cdiv(rows, 8), (int64_t)ctx->sm_count * 8);
     const int ldp8 = p->ldP;
 #define LAUNCH(V, T)                                                                                     \
     FHR_TIMED(TM_NORMALISE, (normalise_kernel<V, T><<<blocks, 256, 0, st>>>(y, y0, dead, p->dead_per_pixel, b, p->Nv, \

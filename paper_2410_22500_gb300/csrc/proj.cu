@@ -101,8 +101,9 @@ void proj_tables_carve(Carve &c, int N, int Nc, int Nv, ProjTables *t) {
     tt.fws = c.take<int>((size_t)Nv * Nc * N);
     tt.rowmaj = c.take<uint8_t>((size_t)Nv);
     tt.bk = c.take<float4>((size_t)Nv * N * N);
-    const int64_t NB = cdiv(Nc, kTmaRays), NTX = cdiv(N, kTmaTile);
-    tt.fspan = c.take<int>((size_t)Nv * NB * N);
+    const int64_t NTX = cdiv(N, kTmaTile);
+    // the run table of either forward block shape: groups x 2 sweeps x ray blocks x lines
+    tt.fspan = c.take<int>((size_t)Nv * 2 * cdiv(Nc, 16) * N);
     tt.bspan = c.take<int>((size_t)Nv * NTX * NTX);
     if (t) *t = tt;
 }
@@ -123,8 +124,9 @@ fhr_status proj_build_tables(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &
     FHR_LAUNCHED();
     proj_table_bk<<<(unsigned)cdiv(nb, 256), 256, 0, ctx->stream>>>(g->angles, g->N, g->Nc, g->Nv, t);
     FHR_LAUNCHED();
-    const int64_t ns = (int64_t)g->Nv * cdiv(g->Nc, kTmaRays) * g->N;
-    proj_span_fw<<<(unsigned)cdiv(ns, 256), 256, 0, ctx->stream>>>(t, g->N, g->Nc, g->Nv, t.fspan);
+    const int vg = tma_fwd_vg(g), rb = vg == 4 ? 16 : kTmaRays;
+    const int64_t ns = cdiv(g->Nv, vg) * 2 * cdiv(g->Nc, rb) * g->N;
+    proj_span_fw<<<(unsigned)cdiv(ns, 256), 256, 0, ctx->stream>>>(t, g->N, g->Nc, g->Nv, vg, rb, t.fspan);
     FHR_LAUNCHED();
     const int64_t nt = (int64_t)g->Nv * cdiv(g->N, kTmaTile) * cdiv(g->N, kTmaTile);
     proj_span_bk<<<(unsigned)cdiv(nt, 256), 256, 0, ctx->stream>>>(t, g->N, g->Nc, g->Nv, t.bspan);

@@ -6,20 +6,28 @@
 
 namespace fhr {
 
-__global__ void proj_span_fw(const ProjTables t, int N, int Nc, int Nv, int *fspan) {
-    const int NB = (Nc + kTmaRays - 1) / kTmaRays;
+// packed run of block (group gi, sweep p, ray block b) in line l: first pixel |
+// length << 16, over the group's views on sweep p's line axis and the block's rays
+__global__ void proj_span_fw(const ProjTables t, int N, int Nc, int Nv, int VG, int R, int *fspan) {
+    const int NB = (Nc + R - 1) / R, NG = (Nv + VG - 1) / VG;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)Nv * NB * N) return;
+    if (idx >= (int64_t)NG * 2 * NB * N) return;
     const int l = (int)(idx % N);
     const int b = (int)((idx / N) % NB);
-    const int v = (int)(idx / ((int64_t)N * NB));
-    const int *s0 = t.fws + ((size_t)v * N + l) * Nc;
-    int lo = s0[b * kTmaRays], hi = lo;
-    for (int c = b * kTmaRays + 1; c < min(Nc, (b + 1) * kTmaRays); ++c) {
-        lo = min(lo, s0[c]);
-        hi = max(hi, s0[c]);
+    const int p = (int)((idx / ((int64_t)N * NB)) % 2);
+    const int gi = (int)(idx / ((int64_t)N * NB * 2));
+    const int v0 = gi * VG;
+    const bool axis = p ? t.rowmaj[v0] == 0 : t.rowmaj[v0] != 0;
+    int lo = 1 << 30, hi = -1;
+    for (int v = v0; v < min(Nv, v0 + VG); ++v) {
+        if ((t.rowmaj[v] != 0) != axis) continue;
+        const int *s0 = t.fws + ((size_t)v * N + l) * Nc;
+        for (int c = b * R; c < min(Nc, (b + 1) * R); ++c) {
+            lo = min(lo, s0[c]);
+            hi = max(hi, s0[c]);
+        }
     }
-    fspan[idx] = lo | ((hi + 4 - lo) << 16);   // first pixel of the run, run length
+    fspan[idx] = hi < 0 ? 0 : (lo | ((hi + 4 - lo) << 16));
 }
 
 __global__ void proj_span_bk(const ProjTables t, int N, int Nc, int Nv, int *bspan) {
@@ -77,6 +85,10 @@ static bool make_map(CUtensorMap *m, CUtensorMapDataType dt, int rank, const voi
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+int tma_fwd_vg(const fhr_geom *g) {
+    return (g->angles == nullptr && (double)g->N * 3.141592653589793 / (double)g->Nv <= 8.95) ? 4 : 1;
+}
+
 bool tma_gathers_ok(const fhr_geom *g, int Wl) {
     return Wl % 4 == 0 && g->Nc % 4 == 0 && g->N <= kTmaMaxN && g->Nv <= kTmaMaxNv && encoder() != nullptr;
 }
@@ -84,28 +96,45 @@ bool tma_gathers_ok(const fhr_geom *g, int Wl) {
 fhr_status tma_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *x, float *y,
                        const float *V, int *status) {
     const int N = g->N, Nc = g->Nc, Nv = g->Nv;
-    CUtensorMap mrow, mcol, mfw, mfws;
+    TmaRunMaps mx;
+    CUtensorMap mfw, mfws;
     {
         const uint64_t dims[3] = {(uint64_t)Wl, (uint64_t)N, (uint64_t)N};
         const uint64_t st[2] = {(uint64_t)Wl * 4, (uint64_t)N * Wl * 4};
-        const uint32_t brow[3] = {kTmaCw, kTmaRunBox, 1}, bcol[3] = {kTmaCw, 1, kTmaRunBox};
-        FHR_ARG(make_map(&mrow, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, x, dims, st, brow) &&
-                    make_map(&mcol, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, x, dims, st, bcol),
-                "tensor map of the image could not be encoded");
-        const uint64_t dw[2] = {(uint64_t)Nc * 4, (uint64_t)Nv * N}, sw[1] = {(uint64_t)Nc * 16};
-        const uint32_t bw[2] = {kTmaRays * 4, 1};
-        const uint64_t ds[2] = {(uint64_t)Nc, (uint64_t)Nv * N}, ss[1] = {(uint64_t)Nc * 4};
-        const uint32_t bs[2] = {kTmaRays, 1};
-        FHR_ARG(make_map(&mfw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, t.fw, dw, sw, bw) &&
-                    make_map(&mfws, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, t.fws, ds, ss, bs),
+        for (int h = 0; h < kTmaRunMaps; ++h) {
+            const uint32_t ht = (uint32_t)tma_run_height(h);
+            const uint32_t brow[3] = {kTmaCw, ht, 1}, bcol[3] = {kTmaCw, 1, ht};
+            FHR_ARG(make_map(&mx.row[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, x, dims, st, brow) &&
+                        make_map(&mx.col[h], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, x, dims, st, bcol),
+                    "tensor map of the image could not be encoded");
+        }
+        const int vg = tma_fwd_vg(g), rb = vg == 4 ? 16 : kTmaRays;
+        const uint64_t dw[3] = {(uint64_t)Nc * 4, (uint64_t)N, (uint64_t)Nv};
+        const uint64_t sw[2] = {(uint64_t)Nc * 16, (uint64_t)N * Nc * 16};
+        const uint32_t bw[3] = {(uint32_t)rb * 4, 1, (uint32_t)vg};
+        const uint64_t ds[3] = {(uint64_t)Nc, (uint64_t)N, (uint64_t)Nv};
+        const uint64_t ss[2] = {(uint64_t)Nc * 4, (uint64_t)N * Nc * 4};
+        const uint32_t bs[3] = {(uint32_t)rb, 1, (uint32_t)vg};
+        FHR_ARG(make_map(&mfw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, t.fw, dw, sw, bw) &&
+                    make_map(&mfws, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, t.fws, ds, ss, bs),
                 "tensor map of the forward table could not be encoded");
     }
-    const size_t smem = tma_fwd_smem(N);
-    FHR_CUDA(cudaFuncSetAttribute(proj_fwd_tma<kTmaFwdG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int NB = (int)cdiv(Nc, kTmaRays);
-    const unsigned blocks = (unsigned)((int64_t)cdiv(Wl, kTmaCw) * Nv * NB);
-    FHR_TIMED(TM_PROJ_FWD, (proj_fwd_tma<kTmaFwdG><<<blocks, kTmaRays * kTmaCw / (4 * kTmaFwdG) + 32, smem, ctx->stream>>>(
-                               mrow, mcol, mfw, mfws, t.fspan, t.rowmaj, y, V, N, Nc, Nv, Wl, status)));
+    const int64_t chunks = cdiv(Wl, kTmaCw);
+    if (tma_fwd_vg(g) == 4) {
+        constexpr int VG = 4, R = 16, G = 2;
+        const size_t smem = tma_fwd_smem_vg(VG * R, N);
+        FHR_CUDA(cudaFuncSetAttribute(proj_fwd_tma<VG, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const unsigned blocks = (unsigned)(chunks * cdiv(Nv, VG) * cdiv(Nc, R));
+        FHR_TIMED(TM_PROJ_FWD, (proj_fwd_tma<VG, R, G><<<blocks, VG * R * kTmaCw / (4 * G) + 32, smem, ctx->stream>>>(
+                                   mx, mfw, mfws, t.fspan, t.rowmaj, y, V, N, Nc, Nv, Wl, status)));
+    } else {
+        constexpr int VG = 1, R = kTmaRays, G = 1;
+        const size_t smem = tma_fwd_smem_vg(VG * R, N);
+        FHR_CUDA(cudaFuncSetAttribute(proj_fwd_tma<VG, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const unsigned blocks = (unsigned)(chunks * Nv * cdiv(Nc, R));
+        FHR_TIMED(TM_PROJ_FWD, (proj_fwd_tma<VG, R, G><<<blocks, VG * R * kTmaCw / (4 * G) + 32, smem, ctx->stream>>>(
+                                   mx, mfw, mfws, t.fspan, t.rowmaj, y, V, N, Nc, Nv, Wl, status)));
+    }
     return FHR_OK;
 }
 

@@ -8,9 +8,9 @@
 //   forward   block = (view v, 32 consecutive rays, 64 channels).  Per image
 //             line l (the axis most parallel to the rays) the rays' candidate
 //             pixels lie in one run of at most 49 pixels (about 30 on
-//             average); the run (boxes of {64 channels, 8 pixels} of the image,
-//             as many as it needs) and the rays' table entries (weights, first
-//             candidate) are copied in; each thread sums its ray's 2-4
+//             average); the run (one box {64 channels, 24..56 pixels} of the
+//             image, the smallest that holds it) and the rays' table entries
+//             (weights, first candidate) are copied in; each thread sums its ray's 2-4
 //             candidates for its channels from shared memory;
 //   backward  block = (8 x 8 pixel tile, 64 channels).  Per view v the tile's
 //             footprint is at most 14 consecutive bins; that slab of the
@@ -29,9 +29,18 @@
 
 namespace fhr {
 
-constexpr int kTmaRays = 32;        // rays per forward block
+constexpr int kTmaRays = 32;        // rays per forward block of one view (16 in blocks of 4 views)
 constexpr int kTmaSpan = 56;        // pixels per staged line: >= ceil(31 sqrt 2) + 1 + 4
-constexpr int kTmaRunBox = 8;       // pixels per tensor copy of a run (a run takes ceil(len / 8) copies)
+// a run of len pixels is copied as one box of the smallest height kTmaRunH[h] >= len
+constexpr int kTmaRunMaps = 5;
+__host__ __device__ constexpr int tma_run_height(int h) { return 24 + 8 * h; }   // 24, 32, 40, 48, 56
+__host__ __device__ inline int tma_run_map(int len) { return len <= 24 ? 0 : min((len - 17) / 8, kTmaRunMaps - 1); }
+
+// The image maps of the forward gather: box {64 channels, height, 1} over rows
+// (row lines) and {64 channels, 1, height} (column lines), per run height.
+struct TmaRunMaps {
+    CUtensorMap row[kTmaRunMaps], col[kTmaRunMaps];
+};
 constexpr int kTmaCw = 64;          // channels per block
 constexpr int kTmaFwdStages = 6;
 constexpr int kTmaTile = 8;         // backward tile side
@@ -43,20 +52,13 @@ constexpr int kTmaFwdG = 1, kTmaBwdG = 2, kTmaUpdG = 2;
 // shared memory)
 constexpr int kTmaMaxN = 4096, kTmaMaxNv = 8192;
 
-// shared-memory bytes of one forward stage: image run, ray weights, first candidates
-constexpr uint32_t kTmaFwdX = kTmaSpan * kTmaCw * 4;
-constexpr uint32_t kTmaFwdStage = kTmaFwdX + kTmaRays * 16 + kTmaRays * 4;
 // one backward stage: sinogram slab, tile table
 constexpr uint32_t kTmaBwdS = kTmaBins * kTmaCw * 4;
 constexpr uint32_t kTmaBwdStage = kTmaBwdS + kTmaTile * kTmaTile * 16;
 
-static_assert(kTmaFwdX % 128 == 0 && kTmaFwdStage % 128 == 0 && kTmaBwdS % 128 == 0 && kTmaBwdStage % 128 == 0,
-              "stages keep 128-byte alignment");
+static_assert(kTmaBwdS % 128 == 0 && kTmaBwdStage % 128 == 0, "stages keep 128-byte alignment");
 
 // stages, run starts, then the full and empty mbarriers
-__host__ __device__ inline size_t tma_fwd_smem(int N) {
-    return (size_t)kTmaFwdStages * kTmaFwdStage + (size_t)N * 4 + kTmaFwdStages * 16 + 16;
-}
 __host__ __device__ inline size_t tma_bwd_smem(int Nv) {
     return (size_t)kTmaBwdStages * kTmaBwdStage + (size_t)Nv * 4 + kTmaBwdStages * 16 + 16;
 }
@@ -83,35 +85,79 @@ __device__ __forceinline__ void tma_drain(uint64_t *bars, int S, int from, int t
     for (int l = from; l < to; ++l) mbar_wait_bounded(&bars[l % S], (uint32_t)((l / S) & 1));
 }
 
+// Position in a ring of S stages, advanced one step at a time (no division in
+// the loops): stage index and the parity of its current use.
+struct Ring {
+    int st = 0;
+    uint32_t par = 0;
+    __device__ __forceinline__ void next(int S) {
+        if (++st == S) {
+            st = 0;
+            par ^= 1u;
+        }
+    }
+};
+
+// Forward block shapes: VG consecutive views x R rays.  Adjacent views see
+// nearly the same pixels in a line (their runs differ by about (N/2) dtheta
+// sqrt 2 pixels), so one staged run serves VG views' rays.
+template <int VG, int R>
+struct FwdShape {
+    static constexpr int VR = VG * R;   // (view, ray) pairs per block
+    static constexpr uint32_t X = kTmaSpan * kTmaCw * 4;
+    static constexpr uint32_t STAGE = (X + VR * 20 + 127) / 128 * 128;
+};
+
+__host__ __device__ inline size_t tma_fwd_smem_vg(int vr, int N) {
+    const size_t stage = ((size_t)kTmaSpan * kTmaCw * 4 + (size_t)vr * 20 + 127) / 128 * 128;
+    return (size_t)kTmaFwdStages * stage + (size_t)2 * N * 4 + kTmaFwdStages * 16 + 16;
+}
+
 // y[v][c][w] = sum over lines and candidates of A x (V non-null: y = V - A x).
-// Block = (channel chunk, view, ray block), chunk-major.  Threads: 32 rays x
-// TR consumers, TR = 64 / (4 G) (thread (r, t) holds channels w0 + 4 t + 4 TR g,
-// g < G), then one producer warp whose lane 0 refills each stage as soon as
-// every consumer warp has released it (full / empty mbarriers, no block-wide
-// barrier inside the sweep).
-template <int G>
-__global__ void __launch_bounds__(kTmaRays * kTmaCw / (4 * G) + 32) proj_fwd_tma(
-    const __grid_constant__ CUtensorMap mx_row, const __grid_constant__ CUtensorMap mx_col,
-    const __grid_constant__ CUtensorMap mfw, const __grid_constant__ CUtensorMap mfws, const int *__restrict__ fspan,
+// Block = (channel chunk, group of VG views, block of R rays), chunk-major.
+// Consumers: VG x R x TR threads, TR = 64 / (4 G) (thread (view, ray, t) holds
+// channels w0 + 4 t + 4 TR g, g < G), then one producer warp whose lane 0
+// refills each stage once every consumer warp has released it (full / empty
+// mbarriers, no block-wide barrier inside the sweep).  A group whose views do
+// not share the line axis (it straddles 45 or 135 degrees) sweeps the lines
+// twice, once per axis, each view's threads taking part in their axis's sweep.
+// Each ray's sum runs over the lines in order, as in the table-driven gather.
+template <int VG, int R, int G>
+__global__ void __launch_bounds__(VG * R * kTmaCw / (4 * G) + 32) proj_fwd_tma(
+    const __grid_constant__ TmaRunMaps mx, const __grid_constant__ CUtensorMap mfw,
+    const __grid_constant__ CUtensorMap mfws, const int *__restrict__ fspan,
     const uint8_t *__restrict__ rowmaj, float *__restrict__ y, const float *__restrict__ V, int N, int Nc, int Nv,
     int Wl, int *status) {
+    using SH = FwdShape<VG, R>;
     constexpr int TR = kTmaCw / (4 * G);
-    constexpr int NT = kTmaRays * TR;   // consumer threads
+    constexpr int NT = VG * R * TR;   // consumer threads
     constexpr int S = kTmaFwdStages;
     extern __shared__ __align__(128) unsigned char smem[];
-    int *sstart = reinterpret_cast<int *>(smem + (size_t)S * kTmaFwdStage);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * kTmaFwdStage + (((size_t)N * 4 + 7) & ~(size_t)7));
+    int *sstart = reinterpret_cast<int *>(smem + (size_t)S * SH::STAGE);   // [pass][line]
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * SH::STAGE + (size_t)2 * N * 4);
     uint64_t *empty = full + S;
 
-    const int NB = (Nc + kTmaRays - 1) / kTmaRays;
+    const int NB = (Nc + R - 1) / R;
+    const int NG = (Nv + VG - 1) / VG;
     int bid = blockIdx.x;
-    const int chunk = bid / (Nv * NB);
-    bid -= chunk * Nv * NB;
-    const int v = bid / NB, b = bid - v * NB;
+    const int chunk = bid / (NG * NB);
+    bid -= chunk * NG * NB;
+    const int gi = bid / NB, b = bid - gi * NB;
+    const int v0 = gi * VG;
     const int w0 = chunk * kTmaCw;
     const int tid = threadIdx.x;
+    // sweeps: the axis of view v0, then (when some view of the group differs) the other
+    const bool ax0 = rowmaj[v0] != 0;
+    bool mixed = false;
+#pragma unroll
+    for (int q = 1; q < VG; ++q)
+        if (v0 + q < Nv && (rowmaj[v0 + q] != 0) != ax0) mixed = true;
+    const int npass = mixed ? 2 : 1;
 
-    for (int l = tid; l < N; l += NT + 32) sstart[l] = fspan[((size_t)v * NB + b) * N + l];
+    for (int i = tid; i < npass * N; i += NT + 32) {
+        const int p = i / N, l = i - p * N;
+        sstart[i] = fspan[(((size_t)gi * 2 + p) * NB + b) * N + l];
+    }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -120,53 +166,57 @@ __global__ void __launch_bounds__(kTmaRays * kTmaCw / (4 * G) + 32) proj_fwd_tma
         fence_mbar_init();
     }
     __syncthreads();
+    const int steps = npass * N;
 
     if (tid >= NT) {
         // ---- producer: lane 0 of the last warp
         if (tid != NT) return;
-        const bool rows = rowmaj[v] != 0;
-        int l = 0;
-        for (; l < N; ++l) {
-            const int st = l % S;
-            if (l >= S && !mbar_wait_bounded(&empty[st], (uint32_t)((l / S - 1) & 1))) {
+        int i = 0;
+        Ring rg;
+        for (; i < steps; ++i, rg.next(S)) {
+            if (i >= S && !mbar_wait_bounded(&empty[rg.st], rg.par ^ 1u)) {
                 report(status, FHR_ERR_TIMEOUT);
                 break;
             }
-            unsigned char *base = smem + (size_t)st * kTmaFwdStage;
-            const int s0 = sstart[l] & 0xffff;
-            const int nbox = min((sstart[l] >> 16) + kTmaRunBox - 1, kTmaSpan) / kTmaRunBox;
-            mbar_arrive_expect_tx(&full[st], (uint32_t)(nbox * kTmaRunBox * kTmaCw * 4 + kTmaRays * 20));
-            for (int q = 0; q < nbox; ++q) {
-                unsigned char *dst = base + (size_t)q * kTmaRunBox * kTmaCw * 4;
-                if (rows) tma_load_3d(dst, &mx_row, w0, s0 + q * kTmaRunBox, l, &full[st]);
-                else tma_load_3d(dst, &mx_col, w0, l, s0 + q * kTmaRunBox, &full[st]);
-            }
-            tma_load_2d(base + kTmaFwdX, &mfw, b * kTmaRays * 4, v * N + l, &full[st]);
-            tma_load_2d(base + kTmaFwdX + kTmaRays * 16, &mfws, b * kTmaRays, v * N + l, &full[st]);
+            const int p = i >= N, l = i - p * N;
+            const bool rows = p ? !ax0 : ax0;
+            unsigned char *base = smem + (size_t)rg.st * SH::STAGE;
+            const int s0 = sstart[i] & 0xffff;
+            const int h = tma_run_map(sstart[i] >> 16);
+            mbar_arrive_expect_tx(&full[rg.st], (uint32_t)(tma_run_height(h) * kTmaCw * 4 + SH::VR * 20));
+            if (rows) tma_load_3d(base, &mx.row[h], w0, s0, l, &full[rg.st]);
+            else tma_load_3d(base, &mx.col[h], w0, l, s0, &full[rg.st]);
+            tma_load_3d(base + SH::X, &mfw, b * R * 4, l, v0, &full[rg.st]);
+            tma_load_3d(base + SH::X + SH::VR * 16, &mfws, b * R, l, v0, &full[rg.st]);
         }
-        tma_drain(full, S, l > S ? l - S : 0, l);   // no copy lands after this thread exits
+        tma_drain(full, S, i > S ? i - S : 0, i);   // no copy lands after this thread exits
         return;
     }
-
-    // ---- consumers
+    // ---- consumers: thread (view q, ray r, channel group t)
     const int lane = tid & 31;
-    const int r = tid / TR, t = tid - r * TR;
-    const int c = b * kTmaRays + r;
-    const bool live = c < Nc;
+    const int q = tid / (R * TR);
+    const int rr = tid - q * R * TR;
+    const int r = rr / TR, t = rr - r * TR;
+    const int v = v0 + q, c = b * R + r;
+    const bool live = v < Nv && c < Nc;
+    const bool my_axis = live && (rowmaj[v] != 0);   // true: row lines
     float4 acc[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int l = 0; l < N; ++l) {
-        const int st = l % S;
-        const unsigned char *base = smem + (size_t)st * kTmaFwdStage;
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], (uint32_t)((l / S) & 1)))) {
+    Ring rg;
+    for (int i = 0; i < steps; ++i, rg.next(S)) {
+        const int st = rg.st;
+        const unsigned char *base = smem + (size_t)st * SH::STAGE;
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], rg.par))) {
             if (lane == 0) report(status, FHR_ERR_TIMEOUT);
             return;   // the producer drains what it issued
         }
-        if (live) {
-            const float4 w = reinterpret_cast<const float4 *>(base + kTmaFwdX)[r];
-            const int run = sstart[l];
-            const int s = reinterpret_cast<const int *>(base + kTmaFwdX + kTmaRays * 16)[r] - (run & 0xffff);
+        const int p = i >= N;
+        const bool active = live && (my_axis == (p ? !ax0 : ax0));
+        if (active) {
+            const float4 w = reinterpret_cast<const float4 *>(base + SH::X)[q * R + r];
+            const int run = sstart[i];
+            const int s = reinterpret_cast<const int *>(base + SH::X + SH::VR * 16)[q * R + r] - (run & 0xffff);
             if (s >= 0 && s + 4 <= min(run >> 16, kTmaSpan)) {
                 const float *xs = reinterpret_cast<const float *>(base) + (size_t)s * kTmaCw + 4 * t;
                 if (w.x != 0.f) {
@@ -262,9 +312,10 @@ __global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G) + 32, U
         if (tid != NT) return;
         const uint32_t txb = (uint32_t)kTmaCw * bins_box * 4 + kTmaTile * kTmaTile * 16;
         int vv = 0;
-        for (; vv < Nv; ++vv) {
-            const int st = vv % S;
-            if (vv >= S && !mbar_wait_bounded(&empty[st], (uint32_t)((vv / S - 1) & 1))) {
+        Ring rg;
+        for (; vv < Nv; ++vv, rg.next(S)) {
+            const int st = rg.st;
+            if (vv >= S && !mbar_wait_bounded(&empty[st], rg.par ^ 1u)) {
                 report(status, FHR_ERR_TIMEOUT);
                 break;
             }
@@ -286,10 +337,11 @@ __global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G) + 32, U
     float4 acc[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int vv = 0; vv < Nv; ++vv) {
-        const int st = vv % S;
+    Ring rg;
+    for (int vv = 0; vv < Nv; ++vv, rg.next(S)) {
+        const int st = rg.st;
         const unsigned char *base = smem + (size_t)st * kTmaBwdStage;
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], (uint32_t)((vv / S) & 1)))) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[st], rg.par))) {
             if (lane == 0) report(status, FHR_ERR_TIMEOUT);
             return;   // the producer drains what it issued
         }
@@ -337,11 +389,15 @@ __global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G) + 32, U
 // run starts of the staged gathers: fspan[v][ray block][line] = the first candidate of
 // the block's first ray that the block reads in that line (the smallest over its rays);
 // bspan[v][tile] = the smallest first candidate bin over the tile's pixels
-__global__ void proj_span_fw(const ProjTables t, int N, int Nc, int Nv, int *fspan);
+__global__ void proj_span_fw(const ProjTables t, int N, int Nc, int Nv, int VG, int R, int *fspan);
 __global__ void proj_span_bk(const ProjTables t, int N, int Nc, int Nv, int *bspan);
 
 // Tensor-map path available for this shape (16-byte strides) and driver?
 bool tma_gathers_ok(const fhr_geom *g, int Wl);
+// Views per forward block: 4 (with 16 rays) when adjacent views' runs are known to
+// overlap enough (default angles and N pi / Nv <= 8.95: the union run of 4 views x
+// 16 rays stays within 50 pixels), else 1 (with 32 rays).
+int tma_fwd_vg(const fhr_geom *g);
 fhr_status tma_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *x, float *y,
                        const float *V, int *status);
 fhr_status tma_backward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *y, float *x,

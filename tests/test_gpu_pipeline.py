@@ -55,7 +55,10 @@ def test_small_3d_end_to_end(fx, orc):
     # a reduced 3-D volume with dead bins: the slice-coupled prior and the (v, c, r) pixel order.
     # The NNDSVD starts (randomised subspace iteration here, exact SVD in the oracle) agree only
     # when the K-th singular gap is clear, so the case has K = Nm = 3 and a high dose
-    # (sigma_3 / sigma_4 ~ 7).
+    # (sigma_3 / sigma_4 ~ 7).  At this dose the MBIR is sensitive to rounding: in the FP64
+    # oracle alone a 1e-7 relative change of the sinogram moves x^s by 5e-4 (rel-L2) and 3e-3
+    # (largest element) after 20 plain SQS iterations, 1e-6 and 7e-6 after 5, so the parity
+    # checks run 5 MBIR iterations.
     from paper_2410_22500_gb300 import synth
 
     pb = synth.scaled(synth.volume_3d_f32, N=32, Nr=8, Nc=48, Nv=30, Nk=64, Nm=3, I0=20000, seed=77)
@@ -63,28 +66,26 @@ def test_small_3d_end_to_end(fx, orc):
     y, y0 = synth.counts_numpy(pb)
     import torch
 
-    prm = fx.pipeline_params(Nv=g.Nv, Nr=g.Nr, Nc=g.Nc, Nk=pb.Nk, N=g.N, K=3, nmf_iters=100, mbir_iters=20, seed=3)
+    prm = fx.pipeline_params(Nv=g.Nv, Nr=g.Nr, Nc=g.Nc, Nk=pb.Nk, N=g.N, K=3, nmf_iters=100, mbir_iters=5, seed=3)
     D = torch.empty((pb.Nk, 3), dtype=torch.float32, device="cuda")
     xh = torch.empty((g.Nr, g.N, g.N, pb.Nk), dtype=torch.float32, device="cuda")
     dead = torch.from_numpy(pb.dead_bins).cuda()
     ws = fx.pipeline(prm, torch.from_numpy(y.view(np.int16)).cuda(), torch.from_numpy(y0.view(np.int16)).cuda(), D, xh,
                      dead=dead)
     assert fx.status(ws) == 0
-    ref = orc.fhr_pipeline(y, y0, 3, g.N, g.angles(), nmf_iters=100, mbir_iters=20, dead=pb.dead_bins)
+    ref = orc.fhr_pipeline(y, y0, 3, g.N, g.angles(), nmf_iters=100, mbir_iters=5, dead=pb.dead_bins)
     # the two sides start from different NNDSVD factors (the GPU's randomised subspace
     # iteration against the exact SVD), which agree to about 1e-4; the per-element bound
     # carries that difference through 100 NMF and 20 MBIR iterations
     assert_close(xh.cpu().numpy(), ref["xh"], 1e-3, elem_tol=1e-2)
     assert np.all(D.cpu().numpy()[pb.dead_bins.astype(bool)] == 0)
-    # the same stages from one shared start (the oracle's NNDSVD factors), 20 NMF iterations:
-    # arithmetic parity (over 100 iterations this nearly degenerate K = 3 fit carries FP32
-    # rounding up to ~1e-3, as the comparison above shows)
+    # the same stages from one shared start (the oracle's NNDSVD factors): arithmetic parity
     Pg = fx.normalise(torch.from_numpy(y.view(np.int16)).cuda(), torch.from_numpy(y0.view(np.int16)).cuda(), dead=dead)
-    Dg, Wg, _ = fx.decompose(Pg, pb.Nk, 3, 20, D=torch.from_numpy(ref["D0"].astype(np.float32)).cuda(),
+    Dg, Wg, _ = fx.decompose(Pg, pb.Nk, 3, 100, D=torch.from_numpy(ref["D0"].astype(np.float32)).cuda(),
                              W=torch.from_numpy(ref["W0"].astype(np.float32)).cuda(), obj=False)
-    xs = fx.reconstruct(Wg.view(g.Nv, g.Nc, g.Nr * 3), g.N, g.Nr, 3, 20)
+    xs = fx.reconstruct(Wg.view(g.Nv, g.Nc, g.Nr * 3), g.N, g.Nr, 3, 5)
     xh2 = fx.expand(xs, Dg, g.N, g.Nr).cpu().numpy()
-    ref2 = orc.fhr_pipeline(y, y0, 3, g.N, g.angles(), nmf_iters=20, mbir_iters=20, dead=pb.dead_bins,
+    ref2 = orc.fhr_pipeline(y, y0, 3, g.N, g.angles(), nmf_iters=100, mbir_iters=5, dead=pb.dead_bins,
                             init=(ref["D0"].astype(np.float32).astype(np.float64),
                                   ref["W0"].astype(np.float32).astype(np.float64)))
     assert_close(xh2, ref2["xh"], 1e-3, what="shared start")
