@@ -46,6 +46,8 @@ constexpr int kTmaFwdStages = 6;
 constexpr int kTmaTile = 8;         // backward tile side
 constexpr int kTmaBins = 16;        // bins per staged view: >= ceil(7 sqrt 2) + 1 + 3
 constexpr int kTmaBwdStages = 12;
+// candidates of weight 0 skipped (a branch per candidate) or summed (always 0 * x)
+constexpr bool kTmaSkipZero = true;
 // channel groups of 4 per thread: forward, plain backward, backward + SQS update
 constexpr int kTmaFwdG = 1, kTmaBwdG = 2, kTmaUpdG = 2;
 // largest image side and view count of the staged path (their run starts are kept in
@@ -219,21 +221,21 @@ __global__ void __launch_bounds__(VG * R * kTmaCw / (4 * G) + 32) proj_fwd_tma(
             const int s = reinterpret_cast<const int *>(base + SH::X + SH::VR * 16)[q * R + r] - (run & 0xffff);
             if (s >= 0 && s + 4 <= min(run >> 16, kTmaSpan)) {
                 const float *xs = reinterpret_cast<const float *>(base) + (size_t)s * kTmaCw + 4 * t;
-                if (w.x != 0.f) {
+                if (!kTmaSkipZero || w.x != 0.f) {
 #pragma unroll
                     for (int g = 0; g < G; ++g) VecF<4>::fma(acc[g], w.x, *reinterpret_cast<const float4 *>(xs + 4 * TR * g));
                 }
-                if (w.y != 0.f) {
+                if (!kTmaSkipZero || w.y != 0.f) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
                         VecF<4>::fma(acc[g], w.y, *reinterpret_cast<const float4 *>(xs + kTmaCw + 4 * TR * g));
                 }
-                if (w.z != 0.f) {
+                if (!kTmaSkipZero || w.z != 0.f) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
                         VecF<4>::fma(acc[g], w.z, *reinterpret_cast<const float4 *>(xs + 2 * kTmaCw + 4 * TR * g));
                 }
-                if (w.w != 0.f) {
+                if (!kTmaSkipZero || w.w != 0.f) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
                         VecF<4>::fma(acc[g], w.w, *reinterpret_cast<const float4 *>(xs + 3 * kTmaCw + 4 * TR * g));
@@ -350,16 +352,16 @@ __global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G) + 32, U
             const int s = (int)w.w - bstart[vv];
             if (s >= 0 && s <= bins_box - 3) {
                 const float *ys = reinterpret_cast<const float *>(base) + (size_t)s * kTmaCw + 4 * t;
-                if (w.x != 0.f) {
+                if (!kTmaSkipZero || w.x != 0.f) {
 #pragma unroll
                     for (int g = 0; g < G; ++g) VecF<4>::fma(acc[g], w.x, *reinterpret_cast<const float4 *>(ys + 4 * TP * g));
                 }
-                if (w.y != 0.f) {
+                if (!kTmaSkipZero || w.y != 0.f) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
                         VecF<4>::fma(acc[g], w.y, *reinterpret_cast<const float4 *>(ys + kTmaCw + 4 * TP * g));
                 }
-                if (w.z != 0.f) {
+                if (!kTmaSkipZero || w.z != 0.f) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
                         VecF<4>::fma(acc[g], w.z, *reinterpret_cast<const float4 *>(ys + 2 * kTmaCw + 4 * TP * g));

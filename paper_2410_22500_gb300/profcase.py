@@ -21,6 +21,10 @@ at the benchmark's shapes (profile with `-k regex:"proj_fwd|mbir_update" -s 2 -c
 `mbir_volume`: the same at the 256^3 precision form's shapes (N = 256, 256 slices x
 K = 6, 120 views x 256 bins: a 403 MB image and a 189 MB sinogram), three SQS
 iterations with momentum.
+`normalise_expand`: the normalisation of counts shaped like 8 detector rows of the
+256^3 precision form (120 views x 8 rows x 256 columns x 1500 bins, 100 counts per
+bin, to BF16 P: 737 MB in, 737 MB out) and the expansion of 8 slices of that
+volume (256 x 256 x 8 voxels, K = 6, to FP32 x^h: 3.1 GB), two calls each.
 `fmd`: the semi-supervised material decomposition of 1,048,576 voxels (the 3-D
 workload's volume), Ns = Nm = 5, seeded mixtures with 10% of the voxels labelled,
 Nk = 1200; three calls (fmd_region_partials, fmd_finish_T, fmd_gram, fmd_spectra,
@@ -98,6 +102,26 @@ def fbp(calls: int = 3) -> None:
     print("ok")
 
 
+def normalise_expand(Nr: int = 8) -> None:
+    build.build()
+    ctx = fhr.Context(0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    Nv, Nc, Nk, N, K = 120, 256, 1500, 256, 6
+    y = torch.poisson(torch.full((Nv, Nr, Nc, Nk), 60.0, device="cuda"), generator=g).to(torch.int32).to(torch.int16)
+    y0 = torch.poisson(torch.full((Nr, Nc, Nk), 100.0, device="cuda"), generator=g).to(torch.int32).to(torch.int16)
+    for _ in range(2):
+        P = ctx.normalise(y, y0, p_dtype=fhr.BF16)
+    del P, y
+    xs = torch.rand((N, N, Nr * K), device="cuda", generator=g)
+    D = torch.rand((Nk, K), device="cuda", generator=g)
+    for _ in range(2):
+        xh = ctx.expand(xs, D, N, Nr)
+    torch.cuda.synchronize()
+    ctx.close()
+    print("ok")
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "nmf_pass"
     if case == "nmf_pass":
@@ -108,6 +132,8 @@ if __name__ == "__main__":
         mbir()
     elif case == "mbir_volume":
         mbir(3, N=256, Nr=256, K=6, Nv=120, Nc=256)
+    elif case == "normalise_expand":
+        normalise_expand()
     elif case == "fmd":
         fmd()
     elif case == "fbp":
