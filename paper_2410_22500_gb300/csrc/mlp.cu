@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "mlp_tc.h"
 
 namespace fhr {
 
@@ -440,7 +441,10 @@ static bool mma_layers(const fhr_mlp_dims *d, const void *X) {
            ((uintptr_t)X & 15) == 0;
 }
 
-static fhr_status mma_layer(fhr_ctx *ctx, const MmaGemmArgs &g) {
+// layers 1 and 2: the tcgen05 kernel (mlp_tc.cu) when the shape allows it, else warp MMA
+static fhr_status mma_layer(fhr_ctx *ctx, const MmaGemmArgs &g, int *status) {
+    TcGemmArgs t{g.M, g.N, g.Kd, g.A, g.lda, g.B, g.ldb, g.bias, g.Z, g.ldz, g.Act, g.ldact, status};
+    if (mlp_tc_ok(t)) return mlp_tc_layer(ctx, t);
     FHR_CUDA(cudaFuncSetAttribute(mlp_gemm_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kMmaSmem));
     dim3 grid((unsigned)cdiv(g.N, MBN), (unsigned)cdiv(g.M, MBM));
     mlp_gemm_mma<<<grid, 256, kMmaSmem, ctx->stream>>>(g);
@@ -462,14 +466,14 @@ static fhr_status forward_chunk(fhr_ctx *ctx, const fhr_mlp_dims *d, const float
         m.bias = prm + L.ob1;
         m.Z = need_z ? w.Z1 : nullptr; m.ldz = d->H1;
         m.Act = (__nv_bfloat16 *)w.A1; m.ldact = d->H1;
-        FHR_TRY(mma_layer(ctx, m));
+        FHR_TRY(mma_layer(ctx, m, w.status));
         m.N = d->H2; m.Kd = d->H1;
         m.A = (const __nv_bfloat16 *)w.A1; m.lda = d->H1;
         m.B = w.wp2; m.ldb = pad8(d->H1);
         m.bias = prm + L.ob2;
         m.Z = need_z ? w.Z2 : nullptr; m.ldz = d->H2;
         m.Act = (__nv_bfloat16 *)w.A2; m.ldact = d->H2;
-        FHR_TRY(mma_layer(ctx, m));
+        FHR_TRY(mma_layer(ctx, m, w.status));
         GemmArgs g{};
         g.M = (int)rows; g.N = d->K; g.Kd = d->H2;
         g.A = w.A2; g.sai = d->H2; g.sak = 1;

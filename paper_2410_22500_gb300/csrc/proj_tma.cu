@@ -66,10 +66,10 @@ static EncodeTiledFn encoder() {
     return fn;
 }
 
-// A tiled map over a row-major array: dims[0] innermost, strides in bytes of
-// dims 1..rank-1, zero fill outside the array.
-static bool make_map(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *base, const uint64_t *dims,
-                     const uint64_t *strides, const uint32_t *box) {
+bool tma_available() { return encoder() != nullptr; }
+
+bool tma_make_map(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *base, const uint64_t *dims,
+                  const uint64_t *strides, const uint32_t *box, CUtensorMapSwizzle swizzle) {
     EncodeTiledFn enc = encoder();
     if (!enc) return false;
     cuuint64_t d[5], s[4];
@@ -80,9 +80,13 @@ static bool make_map(CUtensorMap *m, CUtensorMapDataType dt, int rank, const voi
         es[i] = 1;
     }
     for (int i = 0; i + 1 < rank; ++i) s[i] = strides[i];
-    return enc(m, dt, (cuuint32_t)rank, const_cast<void *>(base), d, s, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return enc(m, dt, (cuuint32_t)rank, const_cast<void *>(base), d, s, bx, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static bool make_map(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *base, const uint64_t *dims,
+                     const uint64_t *strides, const uint32_t *box) {
+    return tma_make_map(m, dt, rank, base, dims, strides, box);
 }
 
 int tma_fwd_vg(const fhr_geom *g) {
@@ -90,7 +94,7 @@ int tma_fwd_vg(const fhr_geom *g) {
 }
 
 bool tma_gathers_ok(const fhr_geom *g, int Wl) {
-    return Wl % 4 == 0 && g->Nc % 4 == 0 && g->N <= kTmaMaxN && g->Nv <= kTmaMaxNv && encoder() != nullptr;
+    return Wl % 4 == 0 && g->Nc % 4 == 0 && g->N <= kTmaMaxN && g->Nv <= kTmaMaxNv && tma_available();
 }
 
 fhr_status tma_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int Wl, const float *x, float *y,

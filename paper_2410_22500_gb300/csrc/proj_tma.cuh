@@ -23,9 +23,8 @@
 // tensor strides); other shapes keep the table-driven kernels.
 #pragma once
 
-#include <cuda.h>   // CUtensorMap and its enums (types only; the encoder comes from the driver at run time)
-
 #include "mbir.cuh"
+#include "tma.cuh"
 
 namespace fhr {
 
@@ -63,22 +62,6 @@ static_assert(kTmaBwdS % 128 == 0 && kTmaBwdStage % 128 == 0, "stages keep 128-b
 // stages, run starts, then the full and empty mbarriers
 __host__ __device__ inline size_t tma_bwd_smem(int Nv) {
     return (size_t)kTmaBwdStages * kTmaBwdStage + (size_t)Nv * 4 + kTmaBwdStages * 16 + 16;
-}
-
-// ---- tensor copies (PTX): global -> this CTA's shared memory, completion on an mbarrier
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(smem_u32(dst)),
-        "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-        : "memory");
 }
 
 // After a timeout the block stops; before it exits, thread 0 waits (bounded) for
