@@ -30,16 +30,32 @@ struct MbirPrior {
     float T, p;
 };
 
+// PTX approximations (PTX ISA: lg2.approx and ex2.approx within about 2^-22
+// relative, rcp.approx within 1 ulp); the influence weight below only scales
+// the prior's surrogate curvature, so these errors stay near 1e-6 of it.
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // rho'(d)/d of the qGGMRF potential with q = 2:
 //   c0 / (1 + u) * (1 + c1 / (1 + u)),  u = (|d| / (T sx))^(2 - p)
+// (a = 0 gives u = 0 through ex2(-inf) = 0; e = 0 gives u = 1)
 __device__ __forceinline__ float qggmrf_infl(float d, float c0, float inv_tsx, float e, float c1) {
-    float u;
-    if (e == 0.f) u = 1.f;
-    else {
-        const float a = fabsf(d) * inv_tsx;
-        u = a > 0.f ? exp2f(e * log2f(a)) : 0.f;
-    }
-    const float r = 1.f / (1.f + u);
+    const float a = fabsf(d) * inv_tsx;
+    const float u = e == 0.f ? 1.f : ex2_approx(e * lg2_approx(a));
+    const float r = rcp_approx(1.f + u);
     return c0 * r * (1.f + c1 * r);
 }
 
@@ -68,12 +84,14 @@ __device__ __forceinline__ void mbir_update_group(const typename VecF<VW>::T &bp
     if (pr.beta != 0.f) {
         const int dy8[8] = {-1, 1, 0, 0, -1, -1, 1, 1};
         const int dx8[8] = {0, 0, -1, 1, -1, 1, -1, 1};
+        // neighbours outside the image read the pixel itself with weight 0 (adds exact
+        // zeros), so no load sits behind a branch
 #pragma unroll
         for (int n = 0; n < 8; ++n) {
             const int yy = iy + dy8[n], xx = ix + dx8[n];
-            if (yy < 0 || yy >= N || xx < 0 || xx >= N) continue;
-            const float b = pr.beta * (n < 4 ? pr.b_edge : pr.b_diag);
-            const typename VF::T zn = ldv<VW, COH>(z + ((size_t)yy * N + xx) * Wl + w0);
+            const bool in = yy >= 0 && yy < N && xx >= 0 && xx < N;
+            const float b = in ? pr.beta * (n < 4 ? pr.b_edge : pr.b_diag) : 0.f;
+            const typename VF::T zn = ldv<VW, COH>(z + ((size_t)(in ? yy : iy) * N + (in ? xx : ix)) * Wl + w0);
 #pragma unroll
             for (int q = 0; q < VW; ++q) {
                 const int j = (w0 + q) % K;
@@ -84,23 +102,34 @@ __device__ __forceinline__ void mbir_update_group(const typename VecF<VW>::T &bp
             }
         }
         if (Nr > 1) {
+            // slices r - 1 and r + 1 of the same channel (w -+ K); missing ones read the
+            // value itself with weight 0
+            float zlo[VW], zhi[VW];
+#pragma unroll
+            for (int q = 0; q < VW; ++q) {
+                const int w = w0 + q, r = w / K;
+                zlo[q] = ldv<1, COH>(z + (size_t)pix * Wl + (r > 0 ? w - K : w));
+                zhi[q] = ldv<1, COH>(z + (size_t)pix * Wl + (r < Nr - 1 ? w + K : w));
+            }
 #pragma unroll
             for (int q = 0; q < VW; ++q) {
                 const int w = w0 + q;
                 const int j = w % K, r = w / K;
                 const float b = pr.beta * pr.b_slice;
                 const float zq = VF::get(zc, q);
-                if (r > 0) {
-                    const float dl = zq - ldv<1, COH>(z + (size_t)pix * Wl + w - K);
+                {
+                    const float bl = r > 0 ? b : 0.f;
+                    const float dl = zq - zlo[q];
                     const float wt = qggmrf_infl(dl, chp->c0[j], chp->inv_tsx[j], pr.e, pr.c1);
-                    g[q] = fmaf(b * dl, wt, g[q]);
-                    d[q] = fmaf(2.f * b, wt, d[q]);
+                    g[q] = fmaf(bl * dl, wt, g[q]);
+                    d[q] = fmaf(2.f * bl, wt, d[q]);
                 }
-                if (r < Nr - 1) {
-                    const float dl = zq - ldv<1, COH>(z + (size_t)pix * Wl + w + K);
+                {
+                    const float bh = r < Nr - 1 ? b : 0.f;
+                    const float dl = zq - zhi[q];
                     const float wt = qggmrf_infl(dl, chp->c0[j], chp->inv_tsx[j], pr.e, pr.c1);
-                    g[q] = fmaf(b * dl, wt, g[q]);
-                    d[q] = fmaf(2.f * b, wt, d[q]);
+                    g[q] = fmaf(bh * dl, wt, g[q]);
+                    d[q] = fmaf(2.f * bh, wt, d[q]);
                 }
             }
         }

@@ -125,14 +125,14 @@ fhr_status tma_forward(fhr_ctx *ctx, const fhr_geom *g, const ProjTables &t, int
     }
     const int64_t chunks = cdiv(Wl, kTmaCw);
     if (tma_fwd_vg(g) == 4) {
-        constexpr int VG = 4, R = 16, G = 2;
+        constexpr int VG = 4, R = 16, G = kTmaFwdG4;
         const size_t smem = tma_fwd_smem_vg(VG * R, N);
         FHR_CUDA(cudaFuncSetAttribute(proj_fwd_tma<VG, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const unsigned blocks = (unsigned)(chunks * cdiv(Nv, VG) * cdiv(Nc, R));
         FHR_TIMED(TM_PROJ_FWD, (proj_fwd_tma<VG, R, G><<<blocks, VG * R * kTmaCw / (4 * G) + 32, smem, ctx->stream>>>(
                                    mx, mfw, mfws, t.fspan, t.rowmaj, y, V, N, Nc, Nv, Wl, status)));
     } else {
-        constexpr int VG = 1, R = kTmaRays, G = 1;
+        constexpr int VG = 1, R = kTmaRays, G = kTmaFwdG;
         const size_t smem = tma_fwd_smem_vg(VG * R, N);
         FHR_CUDA(cudaFuncSetAttribute(proj_fwd_tma<VG, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const unsigned blocks = (unsigned)(chunks * Nv * cdiv(Nc, R));

@@ -41,14 +41,15 @@ struct TmaRunMaps {
     CUtensorMap row[kTmaRunMaps], col[kTmaRunMaps];
 };
 constexpr int kTmaCw = 64;          // channels per block
-constexpr int kTmaFwdStages = 6;
+constexpr int kTmaFwdStages = 4;
 constexpr int kTmaTile = 8;         // backward tile side
 constexpr int kTmaBins = 16;        // bins per staged view: >= ceil(7 sqrt 2) + 1 + 3
 constexpr int kTmaBwdStages = 12;
 // candidates of weight 0 skipped (a branch per candidate) or summed (always 0 * x)
 constexpr bool kTmaSkipZero = true;
-// channel groups of 4 per thread: forward, plain backward, backward + SQS update
-constexpr int kTmaFwdG = 1, kTmaBwdG = 2, kTmaUpdG = 2;
+// channel groups of 4 per thread: forward (one view per block, four views per
+// block), plain backward, backward + SQS update
+constexpr int kTmaFwdG = 1, kTmaFwdG4 = 4, kTmaBwdG = 2, kTmaUpdG = 2;
 // largest image side and view count of the staged path (their run starts are kept in
 // shared memory)
 constexpr int kTmaMaxN = 4096, kTmaMaxNv = 8192;
@@ -101,7 +102,8 @@ __host__ __device__ inline size_t tma_fwd_smem_vg(int vr, int N) {
 // y[v][c][w] = sum over lines and candidates of A x (V non-null: y = V - A x).
 // Block = (channel chunk, group of VG views, block of R rays), chunk-major.
 // Consumers: VG x R x TR threads, TR = 64 / (4 G) (thread (view, ray, t) holds
-// channels w0 + 4 t + 4 TR g, g < G), then one producer warp whose lane 0
+// G float4 groups of channels: w0 + 4 t + 4 TR g, g < G, the groups' order
+// XOR-permuted between the rays of a quarter-warp), then one producer warp whose lane 0
 // refills each stage once every consumer warp has released it (full / empty
 // mbarriers, no block-wide barrier inside the sweep).  A group whose views do
 // not share the line axis (it straddles 45 or 135 degrees) sweeps the lines
@@ -185,6 +187,14 @@ __global__ void __launch_bounds__(VG * R * kTmaCw / (4 * G) + 32) proj_fwd_tma(
     const int v = v0 + q, c = b * R + r;
     const bool live = v < Nv && c < Nc;
     const bool my_axis = live && (rowmaj[v] != 0);   // true: row lines
+    // channel offsets: the Q rays of a quarter-warp take their channel groups in
+    // XOR-permuted order, so their float4 reads of different staged pixels fall in
+    // disjoint banks
+    constexpr int Q = TR >= 8 ? 1 : 8 / TR;
+    int off[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) off[j] = 4 * t + 4 * TR * (j ^ (r & (Q - 1)));
+    auto chan = [&](int g) { return off[g & (Q - 1)] + 4 * TR * (g & ~(Q - 1)); };
     float4 acc[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -203,25 +213,25 @@ __global__ void __launch_bounds__(VG * R * kTmaCw / (4 * G) + 32) proj_fwd_tma(
             const int run = sstart[i];
             const int s = reinterpret_cast<const int *>(base + SH::X + SH::VR * 16)[q * R + r] - (run & 0xffff);
             if (s >= 0 && s + 4 <= min(run >> 16, kTmaSpan)) {
-                const float *xs = reinterpret_cast<const float *>(base) + (size_t)s * kTmaCw + 4 * t;
+                const float *xs = reinterpret_cast<const float *>(base) + (size_t)s * kTmaCw;
                 if (!kTmaSkipZero || w.x != 0.f) {
 #pragma unroll
-                    for (int g = 0; g < G; ++g) VecF<4>::fma(acc[g], w.x, *reinterpret_cast<const float4 *>(xs + 4 * TR * g));
+                    for (int g = 0; g < G; ++g) VecF<4>::fma(acc[g], w.x, *reinterpret_cast<const float4 *>(xs + chan(g)));
                 }
                 if (!kTmaSkipZero || w.y != 0.f) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
-                        VecF<4>::fma(acc[g], w.y, *reinterpret_cast<const float4 *>(xs + kTmaCw + 4 * TR * g));
+                        VecF<4>::fma(acc[g], w.y, *reinterpret_cast<const float4 *>(xs + kTmaCw + chan(g)));
                 }
                 if (!kTmaSkipZero || w.z != 0.f) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
-                        VecF<4>::fma(acc[g], w.z, *reinterpret_cast<const float4 *>(xs + 2 * kTmaCw + 4 * TR * g));
+                        VecF<4>::fma(acc[g], w.z, *reinterpret_cast<const float4 *>(xs + 2 * kTmaCw + chan(g)));
                 }
                 if (!kTmaSkipZero || w.w != 0.f) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
-                        VecF<4>::fma(acc[g], w.w, *reinterpret_cast<const float4 *>(xs + 3 * kTmaCw + 4 * TR * g));
+                        VecF<4>::fma(acc[g], w.w, *reinterpret_cast<const float4 *>(xs + 3 * kTmaCw + chan(g)));
                 }
             } else {
                 report(status, FHR_ERR_UNSUPPORTED);   // a run wider than the staged box
@@ -233,7 +243,7 @@ __global__ void __launch_bounds__(VG * R * kTmaCw / (4 * G) + 32) proj_fwd_tma(
     if (!live) return;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        const int w = w0 + 4 * t + 4 * TR * g;
+        const int w = w0 + chan(g);
         if (w >= Wl) continue;
         const size_t o = ((size_t)v * Nc + c) * Wl + w;
         float4 a = acc[g];
@@ -319,6 +329,12 @@ __global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G) + 32, U
     const int py = p / kTmaTile, px = p - py * kTmaTile;
     const int iy = ty * kTmaTile + py, ix = tx0 * kTmaTile + px;
     const bool live = iy < N && ix < N;
+    // channel offsets XOR-permuted over the Q pixels of a quarter-warp (as in the forward gather)
+    constexpr int Q = TP >= 8 ? 1 : 8 / TP;
+    int off[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) off[j] = 4 * t + 4 * TP * (j ^ (p & (Q - 1)));
+    auto chan = [&](int g) { return off[g & (Q - 1)] + 4 * TP * (g & ~(Q - 1)); };
     float4 acc[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -334,20 +350,20 @@ __global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G) + 32, U
             const float4 w = reinterpret_cast<const float4 *>(base + kTmaBwdS)[p];
             const int s = (int)w.w - bstart[vv];
             if (s >= 0 && s <= bins_box - 3) {
-                const float *ys = reinterpret_cast<const float *>(base) + (size_t)s * kTmaCw + 4 * t;
+                const float *ys = reinterpret_cast<const float *>(base) + (size_t)s * kTmaCw;
                 if (!kTmaSkipZero || w.x != 0.f) {
 #pragma unroll
-                    for (int g = 0; g < G; ++g) VecF<4>::fma(acc[g], w.x, *reinterpret_cast<const float4 *>(ys + 4 * TP * g));
+                    for (int g = 0; g < G; ++g) VecF<4>::fma(acc[g], w.x, *reinterpret_cast<const float4 *>(ys + chan(g)));
                 }
                 if (!kTmaSkipZero || w.y != 0.f) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
-                        VecF<4>::fma(acc[g], w.y, *reinterpret_cast<const float4 *>(ys + kTmaCw + 4 * TP * g));
+                        VecF<4>::fma(acc[g], w.y, *reinterpret_cast<const float4 *>(ys + kTmaCw + chan(g)));
                 }
                 if (!kTmaSkipZero || w.z != 0.f) {
 #pragma unroll
                     for (int g = 0; g < G; ++g)
-                        VecF<4>::fma(acc[g], w.z, *reinterpret_cast<const float4 *>(ys + 2 * kTmaCw + 4 * TP * g));
+                        VecF<4>::fma(acc[g], w.z, *reinterpret_cast<const float4 *>(ys + 2 * kTmaCw + chan(g)));
                 }
             } else {
                 report(status, FHR_ERR_UNSUPPORTED);   // a footprint wider than the staged slab
@@ -360,7 +376,7 @@ __global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G) + 32, U
     const int pix = iy * N + ix;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        const int w = w0 + 4 * t + 4 * TP * g;
+        const int w = w0 + chan(g);
         if (w >= Wl) continue;
         if constexpr (UPDATE) {
             mbir_update_group<4, false>(acc[g], u.z, u.xprev, xout, u.znext, u.dA, u.chp, u.pr, u.mom_a, N, Nc, Nv,
