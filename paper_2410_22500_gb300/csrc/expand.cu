@@ -134,13 +134,19 @@ static fhr_status launch_expand(fhr_ctx *ctx, const float *xs, const float *D, i
     const int bx = 32 * ((warps + rounds - 1) / rounds);
     const int by = std::max(1, 256 / bx);
     const int64_t nvox = (int64_t)Nr * N * N;
-    const int per_sm = std::max(1, std::min(2048 / (bx * by), (int)((size_t)ctx->max_smem_optin / std::max<size_t>(smem, 1))));
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(nvox, by), (int64_t)ctx->sm_count * per_sm));
     const dim3 block(bx, by);
+    // one resident wave of blocks (grid-stride over voxels): as many as fit on the SMs
+    auto grid = [&](const void *fn, size_t sm) -> int {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, bx * by, sm) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(nvox, by), (int64_t)ctx->sm_count * per_sm));
+    };
     if (rounds <= 2) {   // the dictionary columns fit in registers
 #define GOR(T, V)                                                                                          \
-    FHR_TIMED(TM_EXPAND, (expand_reg_kernel<K, T, V, 2><<<blocks, block, 0, ctx->stream>>>(                \
-                             xs, D, N, Nr, Nk, k0, nk, reinterpret_cast<T *>(xh))))
+    FHR_TIMED(TM_EXPAND, (expand_reg_kernel<K, T, V, 2><<<grid((const void *)expand_reg_kernel<K, T, V, 2>, 0), \
+                                                          block, 0, ctx->stream>>>(xs, D, N, Nr, Nk, k0, nk,    \
+                                                                                   reinterpret_cast<T *>(xh))))
         if (dt == FHR_F32) {
             if (vec) GOR(float, true);
             else GOR(float, false);
@@ -155,8 +161,8 @@ static fhr_status launch_expand(fhr_ctx *ctx, const float *xs, const float *D, i
     do {                                                                                                   \
         auto fn = expand_kernel<K, T, V>;                                                                  \
         FHR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));       \
-        FHR_TIMED(TM_EXPAND, (fn<<<blocks, block, smem, ctx->stream>>>(xs, D, N, Nr, Nk, k0, nk,          \
-                                                                       reinterpret_cast<T *>(xh))));        \
+        FHR_TIMED(TM_EXPAND, (fn<<<grid((const void *)fn, smem), block, smem, ctx->stream>>>(             \
+                                 xs, D, N, Nr, Nk, k0, nk, reinterpret_cast<T *>(xh))));                  \
     } while (0)
     if (dt == FHR_F32) {
         if (vec) GO(float, true);

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
 
     if (role == 2) {
         // ---------------- producer warp: one bulk copy per pixel row.  With LANES, lane r
-        // issues row r (lane 8 the tile's W rows, lane 9 the L2 prefetch), so a tile's
+        // issues row r (lane 8 the tile's W rows), so a tile's
         // copies leave in one warp instruction (the gain for the shorter bf16 rows);
         // otherwise lane 0 alone runs the ring and issues them in turn.
         constexpr bool LANES = MmaProducerLanes<TP>::V;
@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
             if (lane == 0) mbar_arrive_expect_tx(&full[s], (uint32_t)rows * row_bytes + wbytes);
             unsigned char *dst = smem + Lyt.tiles + (size_t)s * stage_bytes;
             const TP *src = reinterpret_cast<const TP *>(a.P) + r0 * a.ldP;
-            const int64_t rp = r0 + (int64_t)S * rstep;
+            // (no L2 prefetch of later tiles: measured 4.82 -> 4.45 ms per pass without it on
+            // 7.86M x 1504 bf16 rows; prefetching two or three rings ahead was slower still)
             if constexpr (LANES) {
                 __syncwarp();
                 if (lane < rows) {
@@ -298,19 +299,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
                     if (wbytes)
                         bulk_g2s(smem + Lyt.wst + (size_t)s * kMmaRows * kMaxK * sizeof(float), a.W + r0 * K, wbytes,
                                  &full[s]);
-                } else if (lane == kMmaRows + 1 && rp < a.Np) {
-                    const int prow = (int)((a.Np - rp) < kMmaRows ? (a.Np - rp) : kMmaRows);
-                    bulk_prefetch_l2(reinterpret_cast<const TP *>(a.P) + rp * a.ldP, (uint32_t)prow * row_bytes);
                 }
             } else {
                 for (int r = 0; r < rows; ++r) bulk_g2s(dst + (size_t)r * RS, src + (size_t)r * a.ldP, row_bytes, &full[s]);
                 if (wbytes)
                     bulk_g2s(smem + Lyt.wst + (size_t)s * kMmaRows * kMaxK * sizeof(float), a.W + r0 * K, wbytes,
                              &full[s]);
-                if (rp < a.Np) {
-                    const int prow = (int)((a.Np - rp) < kMmaRows ? (a.Np - rp) : kMmaRows);
-                    bulk_prefetch_l2(reinterpret_cast<const TP *>(a.P) + rp * a.ldP, (uint32_t)prow * row_bytes);
-                }
             }
             if (++s == S) {
                 s = 0;
@@ -443,7 +437,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int s = grp + 4 * h;
-                const float v = w[s];
+                // w[s] by a static select: indexing w with the lane-dependent s would
+                // place the whole array in local memory for the HALS loop above
+                float v = 0.f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (grp == q) v = w[q + 4 * h];
                 if (F32) {
                     const uint32_t big = tf32_big(v);
                     const uint32_t small = __float_as_uint(v - __uint_as_float(big));

@@ -1,6 +1,6 @@
 // Count normalisation: Eq. (neglogattenuation) with the offset correction of
 // Appendix A (Eq. back_offset).  HBM-bound: 2 bytes of counts in, 4 (f32) or
-// 2 (bf16) bytes of P out per element; the open beam is re-read from L2.
+// 2 (bf16) bytes of P out per element; the open beam is read once.
 #include "common.cuh"
 
 namespace fhr {
@@ -14,7 +14,7 @@ namespace fhr {
 // reads and three additions; larger counts take an FP64 logarithm.
 constexpr int kLnTab = 2048;
 
-__device__ __forceinline__ float2 ln_pair(double n) {
+__device__ __noinline__ float2 ln_pair(double n) {
     const double d = log(n);
     const float hi = (float)d;
     return make_float2(hi, (float)(d - (double)hi));
@@ -88,12 +88,47 @@ __device__ __forceinline__ void store1<float>(float *dst, float p) { *dst = p; }
 template <>
 __device__ __forceinline__ void store1<__nv_bfloat16>(__nv_bfloat16 *dst, float p) { *dst = __float2bfloat16_rn(p); }
 
-// One warp per output pixel row j = (v*Nc + c)*Nr + r at a time (the row's
-// indices decomposed once), its lanes over chunks of 8 bins.  Consecutive warps
-// take the same detector pixel (r, c) in consecutive views, so each open-beam
-// row is read from HBM once and then from L2 (the open beam of a 256 x 256
-// detector with 1500 bins is 197 MB, more than L2).
+// Work unit = (detector pixel (r, c), pass): a warp's lanes take bins
+// [256 pass + 8 lane, +8) of that pixel in every view v.  The open-beam
+// logarithms and the dead mask of those bins are formed once per unit and
+// reused for all Nv views, so y0 is read once and each output element costs one
+// table read.  Output row j = (v Nc + c) Nr + r.
 // VEC: counts rows are 16-byte aligned (Nk % 8 == 0), 8 counts per 16-byte load.
+constexpr int kNormViews = 4;   // views whose counts a lane loads before using them
+
+// Open-beam logarithm of a dead or padding bin: p = -huge - ln y is then
+// clamped to exactly 0 by the max(., 0) below, so the mask costs nothing per view.
+constexpr float kDeadLog = 1e30f;
+
+// 8 bins of one view: p = (ln y0 - ln y) - b, clamped at 0 (a = 8 packed counts).
+template <typename TO>
+__device__ __forceinline__ void normalise_chunk(const float2 *tab, const float2 *o, const uint32_t *a, const float *bv,
+                                                int k0, int Nk, int ldP, TO *dst) {
+    float p[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 h0 = ln_count(tab, a[i] & 0xffffu), h1 = ln_count(tab, a[i] >> 16);
+        p[2 * i] = (o[2 * i].x - h0.x) + (o[2 * i].y - h0.y);
+        p[2 * i + 1] = (o[2 * i + 1].x - h1.x) + (o[2 * i + 1].y - h1.y);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float q = p[i];
+        if (bv && k0 + i < Nk) q -= bv[k0 + i];
+        p[i] = fmaxf(q, 0.f);
+    }
+    if (k0 + 8 <= ldP) store8<TO>(dst, p);
+    else
+        for (int i = 0; i < 8 && k0 + i < ldP; ++i) store1<TO>(dst + i, p[i]);
+}
+
+template <typename TO>
+__device__ __forceinline__ void normalise_view(const float2 *tab, const float2 *o, uint4 w, const float *bv, int k0,
+                                               int Nk, int ldP, TO *dst) {
+    const uint32_t aa[4] = {w.x, w.y, w.z, w.w};
+    normalise_chunk<TO>(tab, o, aa, bv, k0, Nk, ldP, dst);
+}
+
 template <bool VEC, typename TO>
 __global__ void __launch_bounds__(256) normalise_kernel(const uint16_t *__restrict__ y, const uint16_t *__restrict__ y0,
                                                         const uint8_t *__restrict__ dead, int per_pixel,
@@ -102,51 +137,66 @@ __global__ void __launch_bounds__(256) normalise_kernel(const uint16_t *__restri
     __shared__ float2 tab[kLnTab];
     fill_ln_table(tab);
     const int nch = (ldP + 7) / 8;
+    const int npass = (nch + 31) / 32;
     const int lane = threadIdx.x & 31;
-    const int64_t rows = (int64_t)Nv * Nc * Nr;
+    const int64_t units = (int64_t)Nr * Nc * npass;
     const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); m < rows; m += wstride) {
-        const int v = (int)(m % Nv);
-        const int64_t rc = m / Nv;
-        const int r = (int)(rc % Nr);
-        const int c = (int)(rc / Nr);
-        const int64_t j = ((int64_t)v * Nc + c) * Nr + r;
-        const uint16_t *yr = y + (((size_t)v * Nr + r) * Nc + c) * Nk;
-        const uint16_t *y0r = y0 + ((size_t)r * Nc + c) * Nk;
-        const float *bv = b ? b + (size_t)v * Nk : nullptr;
-        TO *prow = P + (size_t)j * ldP;
-        for (int ch = lane; ch < nch; ch += 32) {
-            const int k0 = ch * 8;
-            float p[8];
-            if (VEC && k0 + 8 <= Nk) {
-                const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(yr + k0));
-                const uint4 o = __ldg(reinterpret_cast<const uint4 *>(y0r + k0));
-                const uint32_t aa[4] = {a.x, a.y, a.z, a.w}, oo[4] = {o.x, o.y, o.z, o.w};
+    const size_t vstride = (size_t)Nr * Nc * Nk;   // counts of one view
+    const size_t pstride = (size_t)Nc * Nr * ldP;  // P rows of one view
+    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < units; u += wstride) {
+        const int64_t pix = u / npass;
+        const int ch = (int)(u - pix * npass) * 32 + lane;
+        if (ch >= nch) continue;
+        const int r = (int)(pix % Nr), c = (int)(pix / Nr);
+        const int k0 = ch * 8;
+        const size_t yoff = ((size_t)r * Nc + c) * Nk + k0;   // (r, c, k0) in y0 and in view 0 of y
+        float2 o[8];
+        const bool full = VEC && k0 + 8 <= Nk;
+        if (full) {
+            const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(y0 + yoff));
+            const uint32_t qq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                o[2 * i] = ln_count(tab, qq[i] & 0xffffu);
+                o[2 * i + 1] = ln_count(tab, qq[i] >> 16);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) o[i] = ln_count(tab, k0 + i < Nk ? y0[yoff + i] : 1u);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (k0 + i >= Nk || is_dead(dead, per_pixel, r, c, Nc, Nk, k0 + i)) o[i] = make_float2(-kDeadLog, 0.f);
+        TO *prow = P + ((size_t)c * Nr + r) * ldP + k0;   // view 0's row
+        int v = 0;
+        if (full) {
+            for (; v + kNormViews <= Nv; v += kNormViews) {
+                uint4 a[kNormViews];
+#pragma unroll
+                for (int j = 0; j < kNormViews; ++j)
+                    a[j] = __ldcs(reinterpret_cast<const uint4 *>(y + (size_t)(v + j) * vstride + yoff));
+#pragma unroll
+                for (int j = 0; j < kNormViews; ++j)
+                    normalise_view<TO>(tab, o, a[j], b ? b + (size_t)(v + j) * Nk : nullptr, k0, Nk, ldP,
+                                       prow + (size_t)(v + j) * pstride);
+            }
+            for (; v < Nv; ++v) {
+                const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(y + (size_t)v * vstride + yoff));
+                normalise_view<TO>(tab, o, a, b ? b + (size_t)v * Nk : nullptr, k0, Nk, ldP, prow + (size_t)v * pstride);
+            }
+        } else {
+            for (; v < Nv; ++v) {
+                const uint16_t *yr = y + (size_t)v * vstride + yoff;
+                uint32_t aa[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    p[2 * i] = neglog(tab, aa[i] & 0xffffu, oo[i] & 0xffffu);
-                    p[2 * i + 1] = neglog(tab, aa[i] >> 16, oo[i] >> 16);
+                    const uint32_t lo = k0 + 2 * i < Nk ? yr[2 * i] : 1u;
+                    const uint32_t hi = k0 + 2 * i + 1 < Nk ? yr[2 * i + 1] : 1u;
+                    aa[i] = lo | (hi << 16);
                 }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int k = k0 + i;
-                    p[i] = k < Nk ? neglog(tab, yr[k], y0r[k]) : 0.f;
-                }
+                normalise_chunk<TO>(tab, o, aa, b ? b + (size_t)v * Nk : nullptr, k0, Nk, ldP,
+                                           prow + (size_t)v * pstride);
             }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int k = k0 + i;
-                float q = p[i];
-                if (bv && k < Nk) q -= bv[k];
-                q = fmaxf(q, 0.f);
-                if (k >= Nk || is_dead(dead, per_pixel, r, c, Nc, Nk, k)) q = 0.f;
-                p[i] = q;
-            }
-            TO *dst = prow + k0;
-            if (k0 + 8 <= ldP) store8<TO>(dst, p);
-            else
-                for (int i = 0; i < 8 && k0 + i < ldP; ++i) store1<TO>(dst + i, p[i]);
         }
     }
 }
@@ -180,8 +230,8 @@ extern "C" fhr_status fhr_normalise(fhr_ctx *ctx, const fhr_norm_params *p, cons
     // the 8-bin chunks of the f32 output need ldP % 8 == 0 for full 32-byte stores;
     // other ldP take the scalar store tail
     const bool vec = (p->Nk % 8 == 0) && aligned(y, 16) && aligned(y0, 16);
-    const int64_t rows = (int64_t)p->Nv * p->Nc * p->Nr;
-    const int blocks = (int)std::min<int64_t>(cdiv(rows, 8), (int64_t)ctx->sm_count * 8);
+    const int64_t units = (int64_t)p->Nr * p->Nc * cdiv(cdiv(p->ldP, 8), 32);
+    const int blocks = (int)std::min<int64_t>(cdiv(units, 8), (int64_t)ctx->sm_count * 8);
     const int ldp8 = p->ldP;
 #define LAUNCH(V, T)                                                                                     \
     FHR_TIMED(TM_NORMALISE, (normalise_kernel<V, T><<<blocks, 256, 0, st>>>(y, y0, dead, p->dead_per_pixel, b, p->Nv, \

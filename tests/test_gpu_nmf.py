@@ -122,7 +122,7 @@ def test_nndsvd_then_iterations_reach_oracle_objective(fx, orc):
     assert abs(obj.cpu().numpy()[-1] - objr[-1]) <= 1e-3 * objr[-1]
 
 
-def test_full_size_one_iteration_sampled(fx, orc):
+def test_full_size_one_iteration(fx, orc):
     # the 3-D workload at full size (737,280 pixels x 1200 bins, K = 5): one iteration from a
     # GIVEN start; every pixel row of W against the oracle's V half-step, D against the
     # oracle's D half-step over all pixels
