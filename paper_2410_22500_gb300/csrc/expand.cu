@@ -68,14 +68,19 @@ __global__ void __launch_bounds__(256) expand_kernel(const float *__restrict__ x
     }
 }
 
+// voxels per batch of the register-dictionary kernel (their coefficients staged together)
+constexpr int kExpandBatch = 64;
+
 // The same with the dictionary in registers: a thread keeps the columns of its (at
 // most R) chunks for every voxel it visits, so the inner loop reads no shared memory
 // (with the slab in shared memory, the K x 4 floats read per 4-bin chunk outweighed
 // the chunk's own output write).  Slabs of up to R x 256 chunks (1024 R bins).
+
 template <int K, typename TO, bool VEC, int R>
-__global__ void __launch_bounds__(256) expand_reg_kernel(const float *__restrict__ xs, const float *__restrict__ D,
+__global__ void __launch_bounds__(512) expand_reg_kernel(const float *__restrict__ xs, const float *__restrict__ D,
                                                          int N, int Nr, int Nk, int k0, int nk,
                                                          TO *__restrict__ xh) {
+    __shared__ float cs[2][kExpandBatch * K];
     const int nch = (nk + 3) / 4;
     float d[R][K][4];
 #pragma unroll
@@ -88,40 +93,53 @@ __global__ void __launch_bounds__(256) expand_reg_kernel(const float *__restrict
     }
     const int64_t NN = (int64_t)N * N, nvox = (int64_t)Nr * NN;
     const int Wl = Nr * K;
-    const int64_t vstep = (int64_t)gridDim.x * blockDim.y;
-    // the K coefficients of voxel (r, iy, ix); the next voxel's are loaded before
-    // this one's row is written, so their latency hides behind the stores
-    auto coef = [&](int64_t vox, float (&x)[K]) {
+    // batches of V consecutive voxels (r, iy, ix) (a multiple of the block's rows): a
+    // batch's V x K coefficients are loaded one per thread a whole batch ahead and
+    // staged in shared memory, so no row write waits on a coefficient load
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    const int V = min(kExpandBatch, (nt / K) / (int)blockDim.y * (int)blockDim.y);
+    const int64_t nbatch = (nvox + V - 1) / V;
+    auto load = [&](int64_t b) -> float {
+        if (tid >= V * K) return 0.f;
+        const int64_t vox = b * V + tid / K;
+        if (vox >= nvox) return 0.f;
         const int rs = (int)(vox / NN);
-        const float *a = xs + (vox - rs * NN) * Wl + rs * K;
-#pragma unroll
-        for (int j = 0; j < K; ++j) x[j] = __ldg(a + j);
+        return __ldg(xs + (vox - rs * NN) * Wl + rs * K + tid % K);
     };
-    int64_t vox = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
-    float xn[K];
-    if (vox < nvox) coef(vox, xn);
-    for (; vox < nvox; vox += vstep) {
-        float x[K];
+    int64_t b = blockIdx.x;
+    float cn = b < nbatch ? load(b) : 0.f;
+    int buf = 0;
+    for (; b < nbatch; b += gridDim.x, buf ^= 1) {
+        if (tid < V * K) cs[buf][tid] = cn;
+        __syncthreads();   // (also orders the previous batch's reads of cs[buf ^ 1] before its refill)
+        if (b + gridDim.x < nbatch) cn = load(b + gridDim.x);
+        for (int vi = threadIdx.y; vi < V; vi += blockDim.y) {
+            const int64_t vox = b * V + vi;
+            if (vox >= nvox) break;
+            float x[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) x[j] = xn[j];
-        if (vox + vstep < nvox) coef(vox + vstep, xn);
-        TO *row = xh + vox * nk;
+            for (int j = 0; j < K; ++j) x[j] = cs[buf][vi * K + j];
+            TO *row = xh + vox * nk;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int ch = threadIdx.x + r * blockDim.x;
-            if (ch >= nch) break;
-            const int kk = ch * 4;
-            float o[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int r = 0; r < R; ++r) {
+                const int ch = threadIdx.x + r * blockDim.x;
+                if (ch >= nch) break;
+                const int kk = ch * 4;
+                float o[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int j = 0; j < K; ++j)
+                for (int j = 0; j < K; ++j)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) o[e] = fmaf(x[j], d[r][j][e], o[e]);
-            if (VEC) st4<TO>(row + kk, o[0], o[1], o[2], o[3]);
-            else
-                for (int e = 0; e < 4 && kk + e < nk; ++e) st1<TO>(row + kk + e, o[e]);
+                    for (int e = 0; e < 4; ++e) o[e] = fmaf(x[j], d[r][j][e], o[e]);
+                if (VEC) st4<TO>(row + kk, o[0], o[1], o[2], o[3]);
+                else
+                    for (int e = 0; e < 4 && kk + e < nk; ++e) st1<TO>(row + kk + e, o[e]);
+            }
         }
     }
 }
+
+// most warps per voxel row (a block of 32 kExpandWarps threads at most)
+constexpr int kExpandWarps = 8;
 
 template <int K>
 static fhr_status launch_expand(fhr_ctx *ctx, const float *xs, const float *D, int N, int Nr, int Nk, int k0,
@@ -129,8 +147,9 @@ static fhr_status launch_expand(fhr_ctx *ctx, const float *xs, const float *D, i
     const bool vec = (nk % 4 == 0) && aligned(xh, 16);
     const int nch = (nk + 3) / 4;
     const size_t smem = sizeof(float) * (size_t)nch * 4 * K;
-    // threads per voxel: whole warps, at most 8, covering the chunks in as few rounds as possible
-    const int warps = (nch + 31) / 32, rounds = (warps + 7) / 8;
+    // threads per voxel: whole warps, at most kExpandWarps, covering the chunks in as few
+    // rounds as possible
+    const int warps = (nch + 31) / 32, rounds = (warps + kExpandWarps - 1) / kExpandWarps;
     const int bx = 32 * ((warps + rounds - 1) / rounds);
     const int by = std::max(1, 256 / bx);
     const int64_t nvox = (int64_t)Nr * N * N;
@@ -140,20 +159,26 @@ static fhr_status launch_expand(fhr_ctx *ctx, const float *xs, const float *D, i
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, bx * by, sm) != cudaSuccess || per_sm < 1)
             per_sm = 1;
-        return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(nvox, by), (int64_t)ctx->sm_count * per_sm));
+        return (int)std::max<int64_t>(1, std::min<int64_t>(cdiv(nvox, by), (int64_t)ctx->sm_count * per_sm));   // (an upper bound on the batches too)
     };
     if (rounds <= 2) {   // the dictionary columns fit in registers
-#define GOR(T, V)                                                                                          \
-    FHR_TIMED(TM_EXPAND, (expand_reg_kernel<K, T, V, 2><<<grid((const void *)expand_reg_kernel<K, T, V, 2>, 0), \
+#define GOR(T, V, R)                                                                                       \
+    FHR_TIMED(TM_EXPAND, (expand_reg_kernel<K, T, V, R><<<grid((const void *)expand_reg_kernel<K, T, V, R>, 0), \
                                                           block, 0, ctx->stream>>>(xs, D, N, Nr, Nk, k0, nk,    \
                                                                                    reinterpret_cast<T *>(xh))))
+#define GOR2(T, V)           \
+    if (rounds == 1)         \
+        GOR(T, V, 1);        \
+    else                     \
+        GOR(T, V, 2)
         if (dt == FHR_F32) {
-            if (vec) GOR(float, true);
-            else GOR(float, false);
+            if (vec) GOR2(float, true);
+            else GOR2(float, false);
         } else {
-            if (vec) GOR(__nv_bfloat16, true);
-            else GOR(__nv_bfloat16, false);
+            if (vec) GOR2(__nv_bfloat16, true);
+            else GOR2(__nv_bfloat16, false);
         }
+#undef GOR2
 #undef GOR
         return FHR_OK;
     }

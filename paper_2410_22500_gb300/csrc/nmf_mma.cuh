@@ -20,7 +20,9 @@
 // The update warps and the producer sit on one SM sub-partition (warps w and
 // w + 4k share one), with a single consumer warp when there are two update
 // warps and none when there are three, since the update is latency-bound;
-// with LAG = 2 its latency is off the per-tile critical path.
+// phase 3 runs LAG tiles behind phase 1 (1 for f32 rows, 3 for bf16) so that
+// latency is off the per-tile critical path.  The pass is bound by the tiles in
+// flight: a stage is free for the next copy only after phase 3 of its tile.
 //
 // Precision.  f32 P: TF32 products with the three-term split x = big + small
 // (big = x rounded or truncated to TF32, small = x - big) for P, D and w,

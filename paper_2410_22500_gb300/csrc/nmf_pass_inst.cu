@@ -36,13 +36,14 @@ PassFn<__nv_bfloat16> pick<__nv_bfloat16>(int K, int cpt) {
 }
 #undef CASE
 
-// pipeline lag of the tensor-core pass: phase 3 two tiles behind phase 1 for f32
-// rows (the ring still holds two tiles in flight for rows up to ~1300 bins), three
-// for bf16 rows, whose three update warps then each have three tile periods for
-// their HALS step (4.865 -> 4.813 ms per pass on 7.86M x 1504 rows)
+// pipeline lag of the tensor-core pass: phase 3 one tile behind phase 1 for f32
+// rows (their ring holds only five 39 KB stages, so every stage not held for phase 3
+// is one more tile in flight: 0.705 -> 0.693 ms on 737,280 x 1200 rows), three for
+// bf16 rows, whose three update warps then each have three tile periods for their
+// HALS step (a lag of two measured the same; one exceeds the update's latency)
 template <typename TP>
 struct MmaLag {
-    static constexpr int V = sizeof(TP) == 2 ? 3 : 2;
+    static constexpr int V = sizeof(TP) == 2 ? 3 : 1;
 };
 
 template <typename TP>

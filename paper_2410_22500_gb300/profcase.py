@@ -5,6 +5,7 @@
     python -m paper_2410_22500_gb300.profcase mbir
     python -m paper_2410_22500_gb300.profcase fmd
     python -m paper_2410_22500_gb300.profcase fbp
+    python -m paper_2410_22500_gb300.profcase mlp [M]
 
 `nmf_pass`: P of Np x 1200 uniform f32 (default Np = 92,160: 442 MB, larger than
 L2), K = 5, three fast-HALS iterations from a fixed start.  Launch 0 is the first
@@ -29,6 +30,10 @@ volume (256 x 256 x 8 voxels, K = 6, to FP32 x^h: 3.1 GB), two calls each.
 workload's volume), Ns = Nm = 5, seeded mixtures with 10% of the voxels labelled,
 Nk = 1200; three calls (fmd_region_partials, fmd_finish_T, fmd_gram, fmd_spectra,
 fmd_subset_inverses, fmd_nnls each).
+
+`mlp`: the learned start's network forward (1500 -> 256 -> 128 -> 6, bf16 rows of
+1504 bins and bf16 weights) on M rows (default 131,072: 394 MB of rows, 1024 row
+tiles), three calls: launches of mlp_gemm_tc (layers 1 and 2) and the small last layer.
 
 `fbp`: FBP of the 3-D workload's subspace sinograms (N = 128, 64 slices x K = 5, 90
 views x 128 bins; uniform random sinogram), three calls (fbp_filter_kernel, then
@@ -122,6 +127,27 @@ def normalise_expand(Nr: int = 8) -> None:
     print("ok")
 
 
+def mlp(M: int = 131072, calls: int = 3) -> None:
+    import math
+
+    build.build()
+    ctx = fhr.Context(0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    Nk, H1, H2, K, ldx = 1500, 256, 128, 6, 1504
+    sizes = [H1 * Nk, H1, H2 * H1, H2, K * H2, K]
+    scales = [1 / math.sqrt(Nk), 0.1, 1 / math.sqrt(H1), 0.1, 1 / math.sqrt(H2), 0.1]
+    prm = torch.cat([torch.randn(n, device="cuda", generator=g) * sc for n, sc in zip(sizes, scales)])
+    X = (torch.rand((M, ldx), device="cuda", generator=g) * 2).to(torch.bfloat16)
+    d = ctx.mlp_dims(Nk, H1, H2, K, ldx=ldx, x_bf16=True, weights_bf16=True)
+    Y = None
+    for _ in range(calls):
+        Y = ctx.mlp_forward(d, prm, X, Y=Y)
+    torch.cuda.synchronize()
+    ctx.close()
+    print("ok")
+
+
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "nmf_pass"
     if case == "nmf_pass":
@@ -136,6 +162,8 @@ if __name__ == "__main__":
         normalise_expand()
     elif case == "fmd":
         fmd()
+    elif case == "mlp":
+        mlp(int(sys.argv[2]) if len(sys.argv) > 2 else 131072)
     elif case == "fbp":
         fbp()
     else:

@@ -24,7 +24,9 @@ def _rows(P, Nk):
 ATOL, RTOL = 1.5e-7, 2.4e-7
 
 
-@pytest.mark.parametrize("shape", [(3, 2, 5, 16), (4, 3, 7, 37), (2, 1, 48, 128), (1, 1, 1, 8)])
+# Nk % 8 == 0, 4, 2 and odd take the 16-, 8-, 4- and 2-byte count loads
+@pytest.mark.parametrize("shape", [(3, 2, 5, 16), (4, 3, 7, 37), (2, 1, 48, 128), (1, 1, 1, 8), (3, 2, 5, 44),
+                                   (2, 3, 7, 38), (2, 2, 9, 1500)])
 def test_normalise_matches_oracle(fx, orc, shape):
     rng = np.random.default_rng(100 + shape[-1])
     Nv, Nr, Nc, Nk = shape
