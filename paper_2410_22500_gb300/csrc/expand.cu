@@ -127,9 +127,12 @@ __global__ void __launch_bounds__(512) expand_reg_kernel(const float *__restrict
                 const int kk = ch * 4;
                 float o[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int j = 0; j < K; ++j)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) o[e] = fmaf(x[j], d[r][j][e], o[e]);
+                for (int j = 0; j < K; ++j) {   // packed FP32 FMAs, two bins each
+                    const float2 xx = make_float2(x[j], x[j]);
+                    const float2 lo = __ffma2_rn(xx, make_float2(d[r][j][0], d[r][j][1]), make_float2(o[0], o[1]));
+                    const float2 hi = __ffma2_rn(xx, make_float2(d[r][j][2], d[r][j][3]), make_float2(o[2], o[3]));
+                    o[0] = lo.x; o[1] = lo.y; o[2] = hi.x; o[3] = hi.y;
+                }
                 if (VEC) st4<TO>(row + kk, o[0], o[1], o[2], o[3]);
                 else
                     for (int e = 0; e < 4 && kk + e < nk; ++e) st1<TO>(row + kk + e, o[e]);

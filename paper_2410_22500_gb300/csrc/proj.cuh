@@ -27,6 +27,14 @@ struct ProjTables {
     int *bspan;        // [Nv][8 x 8 tiles] first bin of the staged slab
 };
 
+// a += w * x on two lanes at once (the packed FP32 FMA of sm_100 and later; each
+// lane is rounded as a separate fmaf, so the bits are the same)
+__device__ __forceinline__ void fma2(float &a0, float &a1, float w, float x0, float x1) {
+    const float2 r = __ffma2_rn(make_float2(w, w), make_float2(x0, x1), make_float2(a0, a1));
+    a0 = r.x;
+    a1 = r.y;
+}
+
 template <int VW>
 struct VecF;
 template <>
@@ -36,7 +44,8 @@ struct VecF<4> {
     __device__ __forceinline__ static float4 ldca(const float *p) { return __ldca(reinterpret_cast<const float4 *>(p)); }
     __device__ __forceinline__ static void st(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
     __device__ __forceinline__ static void fma(float4 &a, float w, float4 x) {
-        a.x = fmaf(w, x.x, a.x); a.y = fmaf(w, x.y, a.y); a.z = fmaf(w, x.z, a.z); a.w = fmaf(w, x.w, a.w);
+        fma2(a.x, a.y, w, x.x, x.y);
+        fma2(a.z, a.w, w, x.z, x.w);
     }
     __device__ __forceinline__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
     __device__ __forceinline__ static float get(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
