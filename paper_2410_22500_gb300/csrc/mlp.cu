@@ -361,7 +361,7 @@ static MlpLayout mlp_layout(const fhr_mlp_dims *d) {
 }
 
 constexpr int kMlpChunk = 32768;      // pixel rows per training (forward + backward) chunk
-constexpr int kMlpFwdChunk = 65536;   // pixel rows per inference chunk
+constexpr int kMlpFwdChunk = 524288;  // pixel rows per inference chunk (4096 row tiles: 27 per SM)
 constexpr int kSplitRows = 2048;      // contraction rows per split of a weight gradient
 
 struct MlpWs {
@@ -442,6 +442,52 @@ static bool mma_layers(const fhr_mlp_dims *d, const void *X) {
 }
 
 // layers 1 and 2: the tcgen05 kernel (mlp_tc.cu) when the shape allows it, else warp MMA
+constexpr int kOutMax = 8;   // outputs of mlp_out_kernel
+
+// Layer 3 of the tensor-core forward (K <= kOutMax outputs from H2 bf16 activations,
+// H2 % 8 == 0): Y = softplus(A2 W3^T + b3), one pixel row per thread, W3 staged in
+// shared memory as FP32 (every thread reads the same entry: a broadcast).  The
+// 64 x 64 tiles of gemm_kernel would spend most of their work on the K <= 8 columns.
+__global__ void __launch_bounds__(256) mlp_out_kernel(const __nv_bfloat16 *__restrict__ A,
+                                                      const __nv_bfloat16 *__restrict__ W,
+                                                      const float *__restrict__ bias, int H2, int K, int64_t M,
+                                                      float *__restrict__ Y, float *__restrict__ Z3) {
+    extern __shared__ float w3[];   // [K][H2]
+    for (int i = threadIdx.x; i < K * H2; i += blockDim.x) w3[i] = __bfloat162float(W[i]);
+    __syncthreads();
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < M; row += (int64_t)gridDim.x * blockDim.x) {
+        float acc[kOutMax];
+#pragma unroll
+        for (int j = 0; j < kOutMax; ++j) acc[j] = 0.f;
+        const uint4 *a = reinterpret_cast<const uint4 *>(A + row * H2);
+        for (int k = 0; k < H2; k += 8) {
+            const uint4 q = __ldcs(a + k / 8);
+            const uint32_t qq[4] = {q.x, q.y, q.z, q.w};
+            float x[8];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                x[2 * e] = __uint_as_float(qq[e] << 16);
+                x[2 * e + 1] = __uint_as_float(qq[e] & 0xffff0000u);
+            }
+#pragma unroll
+            for (int j = 0; j < kOutMax; ++j) {
+                if (j < K) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc[j] = fmaf(x[e], w3[j * H2 + k + e], acc[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kOutMax; ++j) {
+            if (j < K) {
+                const float v = acc[j] + bias[j];
+                if (Z3) Z3[row * K + j] = v;
+                Y[row * K + j] = softplus_f(v);
+            }
+        }
+    }
+}
+
 static fhr_status mma_layer(fhr_ctx *ctx, const MmaGemmArgs &g, int *status) {
     TcGemmArgs t{g.M, g.N, g.Kd, g.A, g.lda, g.B, g.ldb, g.bias, g.Z, g.ldz, g.Act, g.ldact, status};
     if (mlp_tc_ok(t)) return mlp_tc_layer(ctx, t);
@@ -474,6 +520,15 @@ static fhr_status forward_chunk(fhr_ctx *ctx, const fhr_mlp_dims *d, const float
         m.Z = need_z ? w.Z2 : nullptr; m.ldz = d->H2;
         m.Act = (__nv_bfloat16 *)w.A2; m.ldact = d->H2;
         FHR_TRY(mma_layer(ctx, m, w.status));
+        if (d->H2 % 8 == 0 && d->K <= kOutMax) {
+            const int blocks = (int)std::min<int64_t>(cdiv(rows, 256), (int64_t)ctx->sm_count * 8);
+            const size_t smem = (size_t)d->K * d->H2 * sizeof(float);
+            mlp_out_kernel<<<blocks, 256, smem, ctx->stream>>>((const __nv_bfloat16 *)w.A2,
+                                                              (const __nv_bfloat16 *)wptr<TW>(prm, w, L.oW3),
+                                                              prm + L.ob3, d->H2, d->K, rows, Yout, Z3out);
+            FHR_LAUNCHED();
+            return FHR_OK;
+        }
         GemmArgs g{};
         g.M = (int)rows; g.N = d->K; g.Kd = d->H2;
         g.A = w.A2; g.sai = d->H2; g.sak = 1;
