@@ -149,9 +149,10 @@ def one_slice():
     return synth.scaled(synth.volume_3d_bf16, Nr=1, seed=1002)
 
 
-def algorithmic_pass_bytes(Np, ldP, elem, K_):
-    """One fused NMF pass reads P once and W once, and writes W once."""
-    return Np * ldP * elem + 2 * Np * K_ * 4
+def algorithmic_pass_bytes(Np, Nk, elem, K_):
+    """One fused NMF pass reads the Nk live bins of every row of P once and W once, and
+    writes W once (P's padding columns, streamed too, are not counted)."""
+    return Np * Nk * elem + 2 * Np * K_ * 4
 
 
 def cpu_info():
@@ -401,7 +402,7 @@ def run_ours(args, rank, world, device):
 
     peak, peak_kind = _peaks()
     pass_n, pass_ms = fams["nmf_pass"]
-    pass_bytes = algorithmic_pass_bytes(g.Np, ldP, 2, K)
+    pass_bytes = algorithmic_pass_bytes(g.Np, pb.Nk, 2, K)
     achieved = pass_bytes / (pass_ms / pass_n / 1e3) / 1e9 if pass_n else None
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "nmf_pass_traffic.json")
@@ -409,7 +410,8 @@ def run_ours(args, rank, world, device):
         try:
             with open(tpath) as f:
                 tr = json.load(f)
-            if tr.get("source_digest") == fbuild.kernel_digest("nmf_pass") and tr.get("p_dtype") == "bf16":
+            if (tr.get("source_digest") == fbuild.kernel_digest("nmf_pass") and tr.get("p_dtype") == "bf16"
+                    and tr.get("ldP") == ldP):
                 # scaled from the captured case by rows (traffic grows with the rows streamed)
                 traffic = tr["bytes_per_row"] * g.Np
         except Exception:

@@ -181,6 +181,17 @@ fhr_status fhr_decompose_workspace_size(fhr_ctx *ctx, const fhr_nmf_params *prm,
 fhr_status fhr_decompose(fhr_ctx *ctx, const fhr_nmf_params *prm, const void *P,
                          float *D, float *W, double *obj, void *ws, size_t ws_bytes);
 
+/* Row stride of P (values per row, >= Nk) that the fused pass of fhr_decompose
+ * streams fastest for rows of Nk bins in p_dtype: with it the pass copies each
+ * 8-row tile of P into shared memory as one contiguous transfer instead of one
+ * per row (the tile's shared-memory rows are then exactly the global rows).  The
+ * extra columns must be zero, as fhr_normalise writes them.  When that stride
+ * would pad a row by more than 5 % of Nk, the smallest stride fhr_normalise
+ * accepts (Nk rounded up to 8 values for FHR_BF16, 4 for FHR_F32) is returned
+ * instead.  Host-only: no device is touched.  Errors: FHR_ERR_ARG for Nk < 1, an
+ * unknown p_dtype or a null ldP. */
+fhr_status fhr_nmf_row_stride(int Nk, int p_dtype, int *ldP);
+
 /* The same decomposition without a workspace argument, for callers that
  * cannot allocate device memory or cannot pass a workspace.  Examples: a
  * plugin bound to a fixed C signature, a framework that owns all device

@@ -54,9 +54,9 @@ struct MmaCW {
 };
 constexpr int kMmaWbStride = 48;       // bytes per s-row of the staged w (conflict-free ldmatrix)
 
-// bins per consumer warp (a multiple of 16)
-__host__ __device__ inline int mma_nkw(int ldP, int cw) {
-    const int per = (ldP + cw - 1) / cw;
+// bins per consumer warp (a multiple of 16) for rows of Nk live bins
+__host__ __device__ inline int mma_nkw(int Nk, int cw) {
+    const int per = (Nk + cw - 1) / cw;
     return (per + 15) / 16 * 16;
 }
 
@@ -66,7 +66,7 @@ struct MmaSmem {
 };
 
 // nb: hand-off buffers between phase 1 and phase 3 (pipeline lag + 1)
-__host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stages, int nb, int cw) {
+__host__ __device__ inline MmaSmem mma_smem_layout(int Nk, int esize, int stages, int nb, int cw) {
     MmaSmem L;
     size_t o = 0;
     auto take = [&](size_t bytes, size_t align) {
@@ -75,7 +75,7 @@ __host__ __device__ inline MmaSmem mma_smem_layout(int ldP, int esize, int stage
         o += bytes;
         return r;
     };
-    const size_t cols = (size_t)cw * mma_nkw(ldP, cw);
+    const size_t cols = (size_t)cw * mma_nkw(Nk, cw);
     L.rs = (uint32_t)((cols * esize + 127) / 128 * 128 + 16);
     L.tiles = take((size_t)stages * kMmaRows * L.rs, 128);
     L.wst = take((size_t)stages * kMmaRows * kMaxK * sizeof(float), 128);   // W rows of each staged tile
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
     const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const MmaSmem Lyt = mma_smem_layout(a.ldP, ES, S, NB, CW);
+    const MmaSmem Lyt = mma_smem_layout(a.Nk, ES, S, NB, CW);
     const uint32_t sb = smem_u32(smem);
     const uint32_t tiles_a = sb + (uint32_t)Lyt.tiles;
     const uint32_t wb_a = sb + (uint32_t)Lyt.wb;
@@ -276,7 +276,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
         int64_t i = 0;
         int64_t r0 = (int64_t)blockIdx.x * kMmaRows;
         const int64_t rstep = (int64_t)gridDim.x * kMmaRows;
-        const uint32_t row_bytes = (uint32_t)((size_t)a.ldP * ES);
+        // a staged row holds the bins the consumers read (RS bytes, the first Nk live);
+        // when P's rows are exactly RS bytes apart a full tile is one contiguous copy
+        const uint32_t row_bytes = (uint32_t)min((size_t)a.ldP * ES, (size_t)RS);
+        const bool one_copy = (size_t)a.ldP * ES == (size_t)RS;
         for (; i < my_tiles; ++i, r0 += rstep) {
             bool ok = true;
             if (lane == 0 && i >= S) ok = mbar_wait_bounded(&empty[s], par ^ 1u);
@@ -295,15 +298,22 @@ __global__ void __launch_bounds__(kMmaThreads, 1) nmf_mma_kernel(PassArgs a) {
             // 7.86M x 1504 bf16 rows; prefetching two or three rings ahead was slower still)
             if constexpr (LANES) {
                 __syncwarp();
-                if (lane < rows) {
+                if (one_copy && rows == kMmaRows) {
+                    if (lane == 0) bulk_g2s(dst, src, kMmaRows * RS, &full[s]);
+                } else if (lane < rows) {
                     bulk_g2s(dst + (size_t)lane * RS, src + (size_t)lane * a.ldP, row_bytes, &full[s]);
-                } else if (lane == kMmaRows) {
+                }
+                if (lane == kMmaRows) {
                     if (wbytes)
                         bulk_g2s(smem + Lyt.wst + (size_t)s * kMmaRows * kMaxK * sizeof(float), a.W + r0 * K, wbytes,
                                  &full[s]);
                 }
             } else {
-                for (int r = 0; r < rows; ++r) bulk_g2s(dst + (size_t)r * RS, src + (size_t)r * a.ldP, row_bytes, &full[s]);
+                if (one_copy && rows == kMmaRows)
+                    bulk_g2s(dst, src, kMmaRows * RS, &full[s]);
+                else
+                    for (int r = 0; r < rows; ++r)
+                        bulk_g2s(dst + (size_t)r * RS, src + (size_t)r * a.ldP, row_bytes, &full[s]);
                 if (wbytes)
                     bulk_g2s(smem + Lyt.wst + (size_t)s * kMmaRows * kMaxK * sizeof(float), a.W + r0 * K, wbytes,
                              &full[s]);

@@ -71,16 +71,16 @@ static const void *pick_mma(int nkw) {
     return nullptr;
 }
 
-static fhr_status mma_config(fhr_ctx *ctx, int K, int ldP, int p_dtype, PassConfig *cfg) {
+static fhr_status mma_config(fhr_ctx *ctx, int K, int Nk, int p_dtype, PassConfig *cfg) {
     const int esize = p_dtype == FHR_BF16 ? 2 : 4;
     const int cw = p_dtype == FHR_BF16 ? MmaCW<__nv_bfloat16>::V : MmaCW<float>::V;
-    const void *fn = p_dtype == FHR_BF16 ? pick_mma<__nv_bfloat16>(mma_nkw(ldP, cw)) : pick_mma<float>(mma_nkw(ldP, cw));
+    const void *fn = p_dtype == FHR_BF16 ? pick_mma<__nv_bfloat16>(mma_nkw(Nk, cw)) : pick_mma<float>(mma_nkw(Nk, cw));
     if (!fn) return FHR_ERR_UNSUPPORTED;
     const int nb = (p_dtype == FHR_BF16 ? MmaLag<__nv_bfloat16>::V : MmaLag<float>::V) + 1;
     int stages = 8;
-    while (stages > nb + 1 && mma_smem_layout(ldP, esize, stages, nb, cw).total > (size_t)ctx->max_smem_optin)
+    while (stages > nb + 1 && mma_smem_layout(Nk, esize, stages, nb, cw).total > (size_t)ctx->max_smem_optin)
         --stages;
-    const size_t smem = mma_smem_layout(ldP, esize, stages, nb, cw).total;
+    const size_t smem = mma_smem_layout(Nk, esize, stages, nb, cw).total;
     if (smem > (size_t)ctx->max_smem_optin) return FHR_ERR_UNSUPPORTED;
     FHR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -110,7 +110,7 @@ static size_t pass_smem(int K, int NT, int ldP, int esize, int stages) {
 fhr_status pass_config(fhr_ctx *ctx, int K, int Nk, int ldP, int p_dtype, PassConfig *cfg) {
     cfg->K = K;
     {
-        const fhr_status st = mma_config(ctx, K, ldP, p_dtype, cfg);
+        const fhr_status st = mma_config(ctx, K, Nk, p_dtype, cfg);
         if (st == FHR_OK) return FHR_OK;
         if (st != FHR_ERR_UNSUPPORTED) return st;
     }
@@ -173,3 +173,23 @@ fhr_status launch_pass(fhr_ctx *ctx, const PassConfig &cfg, const PassArgs &a) {
 }
 
 }  // namespace fhr
+
+extern "C" fhr_status fhr_nmf_row_stride(int Nk, int p_dtype, int *ldP) {
+    using namespace fhr;
+    if (Nk < 1 || !ldP || (p_dtype != FHR_F32 && p_dtype != FHR_BF16)) return FHR_ERR_ARG;
+    const bool bf = p_dtype == FHR_BF16;
+    const int mult = bf ? 8 : 4, es = bf ? 2 : 4;
+    const int plain = (Nk + mult - 1) / mult * mult;
+    const int cw = bf ? MmaCW<__nv_bfloat16>::V : MmaCW<float>::V;
+    const int nkw = mma_nkw(Nk, cw);
+    const bool mma = bf ? pick_mma<__nv_bfloat16>(nkw) != nullptr : pick_mma<float>(nkw) != nullptr;
+    int best = plain;
+    if (mma) {
+        const int rs = (int)mma_smem_layout(Nk, es, 2, 2, cw).rs;   // bytes of a staged row
+        const int tile = rs / es;
+        if (rs % es == 0 && tile % mult == 0 && (int64_t)(tile - Nk) * 20 <= Nk) best = tile;
+    }
+    *ldP = best;
+    return FHR_OK;
+}
+

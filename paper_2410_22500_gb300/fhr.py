@@ -25,7 +25,7 @@ ENTRY_POINTS = (
     "fhr_normalise", "fhr_decompose_workspace_size", "fhr_decompose", "fhr_projector_workspace_size",
     "fhr_project", "fhr_backproject", "fhr_reconstruct_workspace_size", "fhr_reconstruct", "fhr_expand",
     "fhr_pipeline_workspace_size", "fhr_pipeline", "fhr_profile_enable", "fhr_profile_read",
-    "fhr_decompose_static", "fhr_decompose_static_status", "fhr_mlp_workspace_size", "fhr_mlp_forward", "fhr_mlp_grad", "fhr_mlp_adamw",
+    "fhr_decompose_static", "fhr_decompose_static_status", "fhr_nmf_row_stride", "fhr_mlp_workspace_size", "fhr_mlp_forward", "fhr_mlp_grad", "fhr_mlp_adamw",
     "fhr_reconstruct_batch_workspace_size", "fhr_reconstruct_batch", "fhr_reconstruct_batch_autotune",
     "fhr_fbp_workspace_size", "fhr_fbp", "fhr_io_join", "fhr_fmd_workspace_size", "fhr_fmd",
     "fhr_snr_workspace_size", "fhr_snr",
@@ -120,6 +120,7 @@ def load():
         L.fhr_pipeline.argtypes = [vp, ctypes.POINTER(PipelineParams), vp, vp, vp, vp, vp, vp, vp, vp, sz]
         L.fhr_decompose_static.argtypes = [vp, ctypes.POINTER(NmfParams), vp, vp, vp, vp]
         L.fhr_decompose_static_status.argtypes = [vp]
+        L.fhr_nmf_row_stride.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.fhr_mlp_workspace_size.argtypes = [vp, ctypes.POINTER(MlpDims), ctypes.c_int, szp]
         L.fhr_mlp_forward.argtypes = [vp, ctypes.POINTER(MlpDims), vp, ctypes.c_int64, vp, vp, vp, sz]
         L.fhr_mlp_grad.argtypes = [vp, ctypes.POINTER(MlpDims), vp, ctypes.c_int64, vp, vp, vp, vp, vp, sz]
@@ -140,6 +141,16 @@ def load():
                                        ctypes.POINTER(ctypes.c_double)]
         _lib = L
         return L
+
+
+def nmf_row_stride(Nk, p_dtype=F32):
+    """fhr_nmf_row_stride: the row stride of P that the fused NMF pass streams fastest."""
+    L = load()
+    out = ctypes.c_int()
+    rc = L.fhr_nmf_row_stride(int(Nk), int(p_dtype), ctypes.byref(out))
+    if rc != OK:
+        raise FhrError(rc, "fhr_nmf_row_stride(%d, %d)" % (Nk, p_dtype))
+    return out.value
 
 
 class FhrError(RuntimeError):
@@ -491,8 +502,7 @@ class Context:
     def pipeline_params(self, *, Nv, Nr, Nc, Nk, N, K, nmf_iters, mbir_iters, p_dtype=F32, xh_dtype=F32,
                         host_io=False, power_iters=0, seed=0, angles=None, init=INIT_NNDSVD, kmeans_samples=0,
                         kmeans_iters=0, recon=RECON_MBIR, dead_per_pixel=False, **mbir_kw):
-        mult = 8 if p_dtype == BF16 else 4
-        ldP = (Nk + mult - 1) // mult * mult
+        ldP = nmf_row_stride(Nk, p_dtype)
         prm = PipelineParams()
         prm.norm = NormParams(Nv, Nr, Nc, Nk, ldP, p_dtype, int(dead_per_pixel))
         prm.nmf = NmfParams(Nv * Nr * Nc, Nk, ldP, K, nmf_iters, init, p_dtype, power_iters, seed, None, None,

@@ -270,7 +270,9 @@ def learned(n_train: int = 2000, rows_per_phantom: int = 2048, target_iters: int
                                     mbir_iters=MBIR_ITERS, momentum=True, p_dtype=p_dtype, xh_dtype=fhr.BF16,
                                     init=init)
         if init == fhr.INIT_LEARNED:
-            prm_p.nmf.mlp = ctypes.addressof(dims)
+            # the network reads the pipeline's own P rows (its row stride)
+            dims_p = ctx.mlp_dims(Nk, H1, H2, K, ldx=prm_p.norm.ldP, x_bf16=True, weights_bf16=True)
+            prm_p.nmf.mlp = ctypes.addressof(dims_p)
             prm_p.nmf.mlp_params = prm.data_ptr()
         ws, wsb = ctx.pipeline_workspace(prm_p)
         ob = torch.empty(max(nmf_iters, 1), dtype=torch.float64, device="cuda")

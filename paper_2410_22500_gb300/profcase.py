@@ -12,8 +12,9 @@ L2), K = 5, three fast-HALS iterations from a fixed start.  Launch 0 is the firs
 pass; profile with `-k regex:nmf_ -s 1 -c 1` (the tensor-core kernel is
 `nmf_mma_kernel`, the CUDA-core one `nmf_pass_kernel`).
 
-`nmf_pass_bf16`: the same with P of Np x 1504 bf16 (default Np = 122,880: 370 MB),
-K = 6, the row length and K of the 256^3 precision form.
+`nmf_pass_bf16`: the same with P of Np rows of 1500 bf16 bins (default Np = 122,880)
+in the row stride fhr_nmf_row_stride gives (1544 values, 380 MB), K = 6: the rows
+and K of the 256^3 precision form as the pipeline lays them out.
 
 `mbir`: the reconstruction of the 3-D workload's subspace sinograms (N = 128,
 64 slices x K = 5, 90 views x 128 bins; uniform random sinogram), four SQS
@@ -46,12 +47,13 @@ import torch
 from . import build, fhr
 
 
-def nmf_pass(Np: int = 92160, Nk: int = 1200, K: int = 5, iters: int = 3, dtype=torch.float32) -> None:
+def nmf_pass(Np: int = 92160, Nk: int = 1200, K: int = 5, iters: int = 3, dtype=torch.float32, ldP=None) -> None:
     build.build()
     ctx = fhr.Context(0)
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
-    P = torch.rand((Np, Nk), device="cuda", generator=g).to(dtype)
+    P = torch.zeros((Np, ldP or Nk), device="cuda", dtype=dtype)
+    P[:, :Nk] = torch.rand((Np, Nk), device="cuda", generator=g).to(dtype)
     D = torch.rand((Nk, K), device="cuda", generator=g) + 0.1
     W = torch.rand((Np, K), device="cuda", generator=g) + 0.1
     ctx.decompose(P, Nk, K, iters, D=D, W=W)
@@ -153,7 +155,8 @@ if __name__ == "__main__":
     if case == "nmf_pass":
         nmf_pass(int(sys.argv[2]) if len(sys.argv) > 2 else 92160)
     elif case == "nmf_pass_bf16":
-        nmf_pass(int(sys.argv[2]) if len(sys.argv) > 2 else 122880, Nk=1504, K=6, dtype=torch.bfloat16)
+        nmf_pass(int(sys.argv[2]) if len(sys.argv) > 2 else 122880, Nk=1500, K=6, dtype=torch.bfloat16,
+                 ldP=fhr.nmf_row_stride(1500, fhr.BF16))
     elif case == "mbir":
         mbir()
     elif case == "mbir_volume":

@@ -47,6 +47,31 @@ def test_first_ten_iterates(fx, orc, Np, Nk, K):
         np.testing.assert_allclose(obj, objr, rtol=1e-4)
 
 
+@pytest.mark.parametrize("dtype,ldP", [("bf16", 200), ("bf16", 256), ("f32", 228)])
+def test_padded_row_stride_matches_oracle(fx, orc, dtype, ldP):
+    # Nk = 96 live bins in rows of ldP: 200 bf16 / 228 f32 values are exactly the staged
+    # row of the tensor-core pass (one bulk copy per 8-row tile), 256 is wider than it
+    # (each row copy stops at the staged row); 500 rows leave a ragged last tile
+    import torch
+    from paper_2410_22500_gb300 import synth
+
+    rng = np.random.default_rng(31)
+    Np, Nk, K = 500, 96, 4
+    P = rng.uniform(0, 1, size=(Np, Nk))
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
+    Pt = torch.zeros((Np, ldP), dtype=tdt)
+    Pt[:, :Nk] = torch.from_numpy(P.astype(np.float32)).to(tdt)
+    Pr = Pt[:, :Nk].float().numpy().astype(np.float64)
+    D0, W0 = synth.nmf_given_init(rng, Np, Nk, K)
+    D0 = D0.astype(np.float32)
+    W0 = W0.astype(np.float32)
+    D, W, obj = fx.decompose(Pt.cuda(), Nk, K, 10, D=_dev(D0), W=_dev(W0))
+    Dr, Wr, objr = orc.nmf(Pr, D0.astype(np.float64), W0.astype(np.float64), 10)
+    assert_close(D.cpu().numpy(), Dr, 1e-4, what="D")
+    assert_close(W.cpu().numpy(), Wr, 1e-4, what="W")
+    np.testing.assert_allclose(obj.cpu().numpy(), objr, rtol=1e-4)
+
+
 def test_tiny_2d_workload_final_objective(fx, orc):
     # the 32x32 / 60-view / Nk=128 / K=3 workload, 200 iterations: final objective within 1e-3
     from paper_2410_22500_gb300 import synth

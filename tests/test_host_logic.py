@@ -71,9 +71,28 @@ def test_bench_algorithmic_pass_bytes():
 
     # the 3-D workload: P (737,280 x 1200 f32) once, W (737,280 x 5 f32) read and written
     assert bench.algorithmic_pass_bytes(737280, 1200, 4, 5) == 737280 * 1200 * 4 + 2 * 737280 * 5 * 4 == 3568435200
-    # the 256^3 precision form: P (7,864,320 x 1504 bf16) once, W (K = 6, f32) read and written
-    assert bench.algorithmic_pass_bytes(7864320, 1504, 2, 6) == 7864320 * 1504 * 2 + 2 * 7864320 * 6 * 4
+    # the 256^3 precision form: the 1500 live bins of P (7,864,320 rows, bf16) once, W (K = 6,
+    # f32) read and written; the row padding P is stored with is not counted
+    assert bench.algorithmic_pass_bytes(7864320, 1500, 2, 6) == 7864320 * 1500 * 2 + 2 * 7864320 * 6 * 4
     assert bench.whole_job_value(4, 10.0, 1000.0) == pytest.approx(40.0)
+
+
+def test_preferred_row_stride():
+    # host-only entry point: the stride whose 8-row tiles are one contiguous copy when it
+    # pads a row by at most 5 %, else Nk rounded up to 8 (bf16) / 4 (f32) values
+    from paper_2410_22500_gb300 import build, fhr
+
+    build.build()
+    assert fhr.nmf_row_stride(1500, fhr.BF16) == 1544    # 12 x 128 bins staged, 3088-byte rows
+    assert fhr.nmf_row_stride(1200, fhr.F32) == 1252     # 13 x 96 bins staged, 5008-byte rows
+    assert fhr.nmf_row_stride(96, fhr.BF16) == 96        # the staged row would double it
+    assert fhr.nmf_row_stride(37, fhr.F32) == 40
+    assert fhr.nmf_row_stride(2000, fhr.BF16) == 2000    # 2120 would pad by 6 %
+    L = fhr.load()
+    import ctypes
+    out = ctypes.c_int()
+    assert L.fhr_nmf_row_stride(0, fhr.BF16, ctypes.byref(out)) == fhr.ERR_ARG
+    assert L.fhr_nmf_row_stride(100, 7, ctypes.byref(out)) == fhr.ERR_ARG
 
 
 def test_bench_cpu_info():
