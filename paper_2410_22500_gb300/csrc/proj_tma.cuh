@@ -50,7 +50,7 @@ constexpr int kTmaBwdStages = 12;
 constexpr bool kTmaSkipZero = true;
 // channel groups of 4 per thread: forward (one view per block, four views per
 // block), plain backward, backward + SQS update
-constexpr int kTmaFwdG = 1, kTmaFwdG4 = 4, kTmaBwdG = 2, kTmaUpdG = 2;
+constexpr int kTmaFwdG = 1, kTmaFwdG4 = 4, kTmaBwdG = 2, kTmaUpdG = 4;
 // largest image side and view count of the staged path (their run starts are kept in
 // shared memory)
 constexpr int kTmaMaxN = 4096, kTmaMaxNv = 8192;
@@ -275,7 +275,10 @@ struct TmaUpdate {
 // chunk-major.  Threads: 64 pixels x TP consumers, TP = 64 / (4 G), then one
 // producer warp (full / empty mbarriers as in the forward gather).
 template <int G, bool UPDATE>
-__global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G) + 32, UPDATE ? 2 : 1) proj_bwd_tma(
+// (the update form with 16 channels per thread, capped at 72 registers for 3 CTAs per SM:
+// 4.86 -> 4.48 ms per iteration on the 256^3 shapes; 8 channels, 2 CTAs of 544 threads
+// before; uncapped, 16 channels fit only 2 CTAs and took 5.0 ms)
+__global__ void __launch_bounds__(kTmaTile * kTmaTile * kTmaCw / (4 * G) + 32, UPDATE ? 3 : 1) proj_bwd_tma(
     const __grid_constant__ CUtensorMap msino, const __grid_constant__ CUtensorMap mbk, const int *__restrict__ bspan,
     float *__restrict__ xout, TmaUpdate u, int N, int Nc, int Nv, int Wl, int bins_box, int *status) {
     constexpr int TP = kTmaCw / (4 * G);
