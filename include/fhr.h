@@ -339,14 +339,22 @@ fhr_status fhr_snr(fhr_ctx *ctx, int64_t Nx, int C, int Nm, int mode, const floa
  * a CUDA graph), two grid-wide phases per iteration (forward residual; fused
  * backward gather + SQS update) separated by bounded grid barriers.
  * probs is a HOST array; each problem's sinogram/volume are device pointers
- * with the layouts of fhr_reconstruct (Wl = Nr*K <= 256; the sinogram 16-byte
+ * with the layouts of fhr_reconstruct (Wl = Nr*K <= 256, or <= 1024 when a
+ * multiple of 4, <= 512 when even; the sinogram 16-byte
  * aligned when Wl % 4 == 0, 8-byte when Wl % 2 == 0); sigma_v[0] > 0 and
  * sigma_x[0] > 0 select explicit per-channel sigmas, else the defaults of
  * fhr_reconstruct.  All problems share the prior parameters and iteration
  * count, and must all be 2-D (Nr = 1) or all 3-D.
- * tile: rays / pixels per work item in block-wide sweeps (0 = 2);
- * fhr_reconstruct_batch_autotune times the candidates {1,2,4,8,16} on the
- * batch (xs is not modified) and returns the fastest.
+ * The projector tile of a work item has two dimensions:
+ *   tile: rays / pixels per work item, in block-wide sweeps (0 = 2);
+ *   vw:   values of a ray's / pixel's channel vector per thread (4, 2 or 1;
+ *         0 = the widest that divides Nr*K), so a block sweeps 256 / (Nr*K/vw)
+ *         rays or pixels at a time.  A problem whose Nr*K the requested vw does
+ *         not divide takes the next smaller width that does.  Results do not
+ *         depend on either (each channel is summed in the same order).
+ * fhr_reconstruct_batch_autotune times every (vw, tile) pair of {4,2,1} x
+ * {1,2,4,8,16} on the batch (xs is not modified; widths no problem can take
+ * are skipped) and returns the fastest pair.
  * ---------------------------------------------------------------------- */
 typedef struct {
     int N, Nr, Nc, Nv, K;
@@ -362,6 +370,7 @@ typedef struct {
     float snr_db;
     int momentum;
     int tile;
+    int vw;
 } fhr_batch_params;
 
 fhr_status fhr_reconstruct_batch_workspace_size(fhr_ctx *ctx, int nprob, const fhr_problem *probs,
@@ -370,7 +379,7 @@ fhr_status fhr_reconstruct_batch(fhr_ctx *ctx, int nprob, const fhr_problem *pro
                                  const fhr_batch_params *prm, void *ws, size_t ws_bytes);
 fhr_status fhr_reconstruct_batch_autotune(fhr_ctx *ctx, int nprob, const fhr_problem *probs,
                                           const fhr_batch_params *prm, void *ws, size_t ws_bytes,
-                                          int *best_tile);
+                                          int *best_tile, int *best_vw);
 
 /* ------------------------------------------------------------------------
  * Subspace expansion -- Eq. (sub_expansion), x^h = x^s (D^s)^T.

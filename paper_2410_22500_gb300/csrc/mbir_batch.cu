@@ -23,6 +23,7 @@ __global__ void fill_kernel(float *x, int64_t n, float v);
 
 struct BatchProb {
     int N, Nc, Nv, Nr, K, Wl;
+    int vw;   // values of the channel vector per thread in the gathers
     ProjTables t;
     const float *sino;
     float *e, *buf[4], *dA;
@@ -77,9 +78,16 @@ __device__ bool grid_barrier(unsigned *bar, int *status) {
 }
 
 // Values per thread for a problem's Wl (all Wl values of a pixel / ray are
-// one contiguous vector; host and device agree on this split).
-__host__ __device__ inline int batch_vw(int Wl) { return Wl % 4 == 0 ? 4 : (Wl % 2 == 0 ? 2 : 1); }
-__host__ __device__ inline int batch_sweep(int Wl) { return kBatchThreads / (Wl / batch_vw(Wl)); }
+// one contiguous vector): the widest of 4, 2, 1 that is at most the requested
+// width (0: no limit) and divides Wl; host and device agree on this split.
+// A width that would need more than a block's threads for one vector is widened.
+__host__ __device__ inline int batch_vw(int Wl, int req = 0) {
+    const int lim = req > 0 ? req : 4;
+    int vw = (lim >= 4 && Wl % 4 == 0) ? 4 : ((lim >= 2 && Wl % 2 == 0) ? 2 : 1);
+    while (vw < 4 && Wl / vw > kBatchThreads && Wl % (2 * vw) == 0) vw *= 2;
+    return vw;
+}
+__host__ __device__ inline int batch_sweep(int Wl, int vw) { return kBatchThreads / (Wl / vw); }
 
 template <int VW>
 __device__ __forceinline__ void batch_forward(const BatchItem &item, const BatchProb &P, const float *z) {
@@ -130,7 +138,7 @@ __global__ void __launch_bounds__(kBatchThreads, 65536 / (kBatchThreads * 64)) m
             const BatchItem item = a.fitems[f];
             const BatchProb &P = a.probs[item.q];
             const float *z = a.momentum ? P.buf[1 + 2 * par] : P.buf[par];
-            const int vw = batch_vw(P.Wl);
+            const int vw = P.vw;
             if (vw == 4) batch_forward<4>(item, P, z);
             else if (vw == 2) batch_forward<2>(item, P, z);
             else batch_forward<1>(item, P, z);
@@ -150,7 +158,7 @@ __global__ void __launch_bounds__(kBatchThreads, 65536 / (kBatchThreads * 64)) m
                 z = P.buf[par];
                 xnew = P.buf[1 - par];
             }
-            const int vw = batch_vw(P.Wl);
+            const int vw = P.vw;
             if (vw == 4) batch_update<4>(item, P, xprev, z, xnew, znext, a.pr, a.mom[it]);
             else if (vw == 2) batch_update<2>(item, P, xprev, z, xnew, znext, a.pr, a.mom[it]);
             else batch_update<1>(item, P, xprev, z, xnew, znext, a.pr, a.mom[it]);
@@ -184,10 +192,12 @@ static size_t prob_bytes(const fhr_problem &q, int K) {
     return c.size();
 }
 
-static int64_t tile_rows(int Wl, int tile) { return (int64_t)tile * batch_sweep(Wl); }
+// rays / pixels per work item; at least one whenever the problem passed check_batch
+// (batch_vw widens vw until a vector fits a block)
+static int64_t tile_rows(int Wl, int vw, int tile) { return (int64_t)tile * std::max(1, batch_sweep(Wl, vw)); }
 
 static size_t carve_batch(void *base, int nprob, const fhr_problem *probs, const fhr_batch_params *p, int tile,
-                          BatchWs *w, std::vector<BatchItem> *fi, std::vector<BatchItem> *bi) {
+                          int vw_req, BatchWs *w, std::vector<BatchItem> *fi, std::vector<BatchItem> *bi) {
     Carve c(base);
     BatchWs t{};
     t.status = c.take<int>(kStatusBytes / sizeof(int));
@@ -195,12 +205,14 @@ static size_t carve_batch(void *base, int nprob, const fhr_problem *probs, const
     t.counter = c.take<unsigned>(4);
     t.sig_part = c.take<double>((size_t)kSigBlocks * 2 * kMbirMaxK);
     t.dprobs = c.take<BatchProb>((size_t)nprob);
-    // work items: enough room for the smallest tile (1)
+    // work items: enough room for the smallest tile (1 sweep at the narrowest width the
+    // problem takes: batch_vw(Wl, 1), widened when Wl exceeds a block's threads)
     int64_t nitems = 0;
     for (int q = 0; q < nprob; ++q) {
         const int Wl = probs[q].Nr * probs[q].K;
-        nitems += cdiv((int64_t)probs[q].Nv * probs[q].Nc, tile_rows(Wl, 1));
-        nitems += cdiv((int64_t)probs[q].N * probs[q].N, tile_rows(Wl, 1));
+        const int64_t tr = tile_rows(Wl, batch_vw(Wl, 1), 1);
+        nitems += cdiv((int64_t)probs[q].Nv * probs[q].Nc, tr);
+        nitems += cdiv((int64_t)probs[q].N * probs[q].N, tr);
     }
     t.items = c.take<BatchItem>((size_t)nitems);
     t.mom = c.take<float>((size_t)std::max(1, p->iters));
@@ -215,7 +227,7 @@ static size_t carve_batch(void *base, int nprob, const fhr_problem *probs, const
         bi->clear();
         for (int q = 0; q < nprob; ++q) {
             const int Wl = probs[q].Nr * probs[q].K;
-            const int64_t tr = tile_rows(Wl, tile);
+            const int64_t tr = tile_rows(Wl, batch_vw(Wl, vw_req), tile);
             const int64_t nr = (int64_t)probs[q].Nv * probs[q].Nc, npx = (int64_t)probs[q].N * probs[q].N;
             for (int64_t s = 0; s < nr; s += tr) fi->push_back({q, (int)s, (int)std::min<int64_t>(tr, nr - s)});
             for (int64_t s = 0; s < npx; s += tr) bi->push_back({q, (int)s, (int)std::min<int64_t>(tr, npx - s)});
@@ -223,8 +235,8 @@ static size_t carve_batch(void *base, int nprob, const fhr_problem *probs, const
         // largest items first (work per item ~ block sweeps x gather length x values per thread)
         auto cost = [&](const BatchItem &it, bool fwd) {
             const fhr_problem &b = probs[it.q];
-            const int Wl = b.Nr * b.K, sw = batch_sweep(Wl);
-            return (int64_t)((it.count + sw - 1) / sw) * (fwd ? b.N : b.Nv + 9) * batch_vw(Wl);
+            const int Wl = b.Nr * b.K, vw = batch_vw(Wl, vw_req), sw = batch_sweep(Wl, vw);
+            return (int64_t)((it.count + sw - 1) / sw) * (fwd ? b.N : b.Nv + 9) * vw;
         };
         std::stable_sort(fi->begin(), fi->end(),
                          [&](const BatchItem &x, const BatchItem &y) { return cost(x, true) > cost(y, true); });
@@ -244,7 +256,9 @@ static fhr_status check_batch(fhr_ctx *ctx, int nprob, const fhr_problem *probs,
         FHR_ARG(b.K >= 1 && b.K <= kMbirMaxK, "problem %d: K must be 1..8", q);
         fhr_geom g{b.N, b.Nr, b.Nc, b.Nv, b.angles};
         FHR_TRY(check_geom(ctx, &g, b.Nr * b.K));
-        FHR_ARG(b.Nr * b.K <= kBatchThreads, "problem %d: Nr*K must be <= %d in a batch", q, kBatchThreads);
+        FHR_ARG(b.Nr * b.K / batch_vw(b.Nr * b.K) <= kBatchThreads,
+                "problem %d: Nr*K must be <= %d in a batch (<= %d when a multiple of 4)", q, kBatchThreads,
+                4 * kBatchThreads);
         FHR_ARG(b.sino && b.xs, "problem %d: null sinogram or volume", q);
         FHR_ARG(aligned(b.sino, 4 * (size_t)batch_vw(b.Nr * b.K)), "problem %d: sinogram not aligned to %d bytes", q,
                 4 * batch_vw(b.Nr * b.K));
@@ -257,14 +271,26 @@ static fhr_status check_batch(fhr_ctx *ctx, int nprob, const fhr_problem *probs,
 }
 
 static fhr_status batch_run(fhr_ctx *ctx, int nprob, const fhr_problem *probs, const fhr_batch_params *p, int tile,
-                            void *ws, size_t ws_bytes, bool write_back, float *ms_out) {
+                            int vw_req, void *ws, size_t ws_bytes, bool write_back, float *ms_out) {
     FHR_TRY(check_batch(ctx, nprob, probs, p));
     FHR_ARG(ws && aligned(ws, 256), "workspace must be non-null and 256-byte aligned");
     FHR_ARG(tile >= 1 && tile <= 64, "tile must be 1..64");
+    FHR_ARG(vw_req == 0 || vw_req == 1 || vw_req == 2 || vw_req == 4, "vw must be 0, 1, 2 or 4");
     BatchWs w;
     std::vector<BatchItem> fi, bi;
-    const size_t need = carve_batch(ws, nprob, probs, p, tile, &w, &fi, &bi);
+    const size_t need = carve_batch(ws, nprob, probs, p, tile, vw_req, &w, &fi, &bi);
     FHR_ARG(ws_bytes >= need, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+    {   // the item lists must fit the array carved for them (sized for the smallest tile)
+        int64_t cap = 0;
+        for (int q = 0; q < nprob; ++q) {
+            const int Wl = probs[q].Nr * probs[q].K;
+            const int64_t tr = tile_rows(Wl, batch_vw(Wl, 1), 1);
+            cap += cdiv((int64_t)probs[q].Nv * probs[q].Nc, tr) + cdiv((int64_t)probs[q].N * probs[q].N, tr);
+        }
+        if ((int64_t)(fi.size() + bi.size()) > cap)
+            return set_error(ctx, FHR_ERR_ARG, "internal: %zu work items for room of %lld", fi.size() + bi.size(),
+                             (long long)cap);
+    }
     FHR_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     FHR_CUDA(cudaMemsetAsync(w.status, 0, kStatusBytes, st));
@@ -286,6 +312,7 @@ static fhr_status batch_run(fhr_ctx *ctx, int nprob, const fhr_problem *probs, c
         fhr_geom g{b.N, b.Nr, b.Nc, b.Nv, b.angles};
         BatchProb &P = hp[(size_t)q];
         P.N = b.N; P.Nc = b.Nc; P.Nv = b.Nv; P.Nr = b.Nr; P.K = b.K; P.Wl = b.Nr * b.K;
+        P.vw = batch_vw(P.Wl, vw_req);
         Carve c(cur);
         proj_tables_carve(c, g.N, g.Nc, g.Nv, &P.t);
         P.chan = c.take<MbirChan>(1);
@@ -409,7 +436,7 @@ extern "C" fhr_status fhr_reconstruct_batch_workspace_size(fhr_ctx *ctx, int npr
     if (!ctx) return FHR_ERR_ARG;
     FHR_TRY(check_batch(ctx, nprob, probs, p));
     FHR_ARG(bytes, "bytes is null");
-    *bytes = carve_batch(nullptr, nprob, probs, p, 1, nullptr, nullptr, nullptr);
+    *bytes = carve_batch(nullptr, nprob, probs, p, 1, 1, nullptr, nullptr, nullptr);
     return FHR_OK;
 }
 
@@ -417,27 +444,37 @@ extern "C" fhr_status fhr_reconstruct_batch(fhr_ctx *ctx, int nprob, const fhr_p
                                             const fhr_batch_params *p, void *ws, size_t ws_bytes) {
     if (!ctx) return FHR_ERR_ARG;
     FHR_ARG(p, "params is null");
-    return batch_run(ctx, nprob, probs, p, p->tile > 0 ? p->tile : 2, ws, ws_bytes, true, nullptr);
+    return batch_run(ctx, nprob, probs, p, p->tile > 0 ? p->tile : 2, p->vw, ws, ws_bytes, true, nullptr);
 }
 
 extern "C" fhr_status fhr_reconstruct_batch_autotune(fhr_ctx *ctx, int nprob, const fhr_problem *probs,
                                                      const fhr_batch_params *p, void *ws, size_t ws_bytes,
-                                                     int *best_tile) {
+                                                     int *best_tile, int *best_vw) {
     if (!ctx) return FHR_ERR_ARG;
-    FHR_ARG(p && best_tile, "null argument");
+    FHR_ARG(p && best_tile && best_vw, "null argument");
+    FHR_TRY(check_batch(ctx, nprob, probs, p));
     fhr_batch_params q = *p;
     q.iters = p->iters > 0 ? std::min(p->iters, 4) : 4;
     float best = 1e30f;
-    int bt = 2;
-    const int cand[] = {1, 2, 4, 8, 16};
-    for (int t : cand) {
-        float ms = 0.f;
-        FHR_TRY(batch_run(ctx, nprob, probs, &q, t, ws, ws_bytes, false, &ms));
-        if (ms < best) {
-            best = ms;
-            bt = t;
+    int bt = 2, bv = 0;
+    const int tiles[] = {1, 2, 4, 8, 16};
+    std::vector<int> prev;   // the per-problem widths of the last width tried
+    for (int vw : {4, 2, 1}) {
+        std::vector<int> eff((size_t)nprob);
+        for (int k = 0; k < nprob; ++k) eff[(size_t)k] = batch_vw(probs[k].Nr * probs[k].K, vw);
+        if (eff == prev) continue;   // no problem takes this width: same shapes as the last
+        prev = eff;
+        for (int t : tiles) {
+            float ms = 0.f;
+            FHR_TRY(batch_run(ctx, nprob, probs, &q, t, vw, ws, ws_bytes, false, &ms));
+            if (ms < best) {
+                best = ms;
+                bt = t;
+                bv = vw;
+            }
         }
     }
     *best_tile = bt;
+    *best_vw = bv;
     return FHR_OK;
 }

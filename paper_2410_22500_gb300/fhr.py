@@ -65,7 +65,7 @@ class Problem(ctypes.Structure):
 class BatchParams(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("p", ctypes.c_float), ("q", ctypes.c_float), ("T", ctypes.c_float),
                 ("beta", ctypes.c_float), ("snr_db", ctypes.c_float), ("momentum", ctypes.c_int),
-                ("tile", ctypes.c_int)]
+                ("tile", ctypes.c_int), ("vw", ctypes.c_int)]
 
 
 class MlpDims(ctypes.Structure):
@@ -128,7 +128,8 @@ def load():
         PP, BP = ctypes.POINTER(Problem), ctypes.POINTER(BatchParams)
         L.fhr_reconstruct_batch_workspace_size.argtypes = [vp, ctypes.c_int, PP, BP, szp]
         L.fhr_reconstruct_batch.argtypes = [vp, ctypes.c_int, PP, BP, vp, sz]
-        L.fhr_reconstruct_batch_autotune.argtypes = [vp, ctypes.c_int, PP, BP, vp, sz, ctypes.POINTER(ctypes.c_int)]
+        L.fhr_reconstruct_batch_autotune.argtypes = [vp, ctypes.c_int, PP, BP, vp, sz, ctypes.POINTER(ctypes.c_int),
+                                                     ctypes.POINTER(ctypes.c_int)]
         L.fhr_io_join.argtypes = [vp]
         L.fhr_fmd_workspace_size.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, szp]
         L.fhr_fmd.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int] + [vp] * 7 + [sz]
@@ -418,35 +419,36 @@ class Context:
         return arr
 
     @staticmethod
-    def batch_params(iters, p=1.2, q=2.0, T=1.0, beta=1.0, snr_db=30.0, momentum=False, tile=0):
-        return BatchParams(iters, p, q, T, beta, snr_db, int(momentum), tile)
+    def batch_params(iters, p=1.2, q=2.0, T=1.0, beta=1.0, snr_db=30.0, momentum=False, tile=0, vw=0):
+        return BatchParams(iters, p, q, T, beta, snr_db, int(momentum), tile, vw)
 
-    def reconstruct_batch(self, sinos, Ns, Ks, iters, *, Nr=1, xss=None, angles=None, sigmas=None, tile=0,
+    def reconstruct_batch(self, sinos, Ns, Ks, iters, *, Nr=1, xss=None, angles=None, sigmas=None, tile=0, vw=0,
                           autotune=False, check_status=True, **kw):
         """Eq. (recon) for every problem of the batch in one persistent launch.
-        Returns (xss, tile used)."""
+        Returns (xss, tile, vw): the work-item size and the values per thread used
+        (vw 0: the widest each problem takes)."""
         torch = _torch()
         Nrs = list(Nr) if isinstance(Nr, (list, tuple)) else [Nr] * len(sinos)
         if xss is None:
             xss = [torch.zeros((N, N, r * K), dtype=torch.float32, device=s.device)
                    for s, N, K, r in zip(sinos, Ns, Ks, Nrs)]
         arr = self.batch_problems(sinos, Ns, Ks, xss, Nr=Nr, angles=angles, sigmas=sigmas)
-        prm = self.batch_params(iters, tile=tile, **kw)
+        prm = self.batch_params(iters, tile=tile, vw=vw, **kw)
         n = ctypes.c_size_t()
         self.check(self.L.fhr_reconstruct_batch_workspace_size(self._h, len(sinos), arr, ctypes.byref(prm),
                                                                ctypes.byref(n)))
         ws = self.workspace(n.value)
         if autotune:
-            best = ctypes.c_int()
+            best, best_vw = ctypes.c_int(), ctypes.c_int()
             self.check(self.L.fhr_reconstruct_batch_autotune(self._h, len(sinos), arr, ctypes.byref(prm), _ptr(ws),
-                                                             n.value, ctypes.byref(best)))
+                                                             n.value, ctypes.byref(best), ctypes.byref(best_vw)))
             if check_status:
                 self.check(self.status(ws))
-            prm.tile = best.value
+            prm.tile, prm.vw = best.value, best_vw.value
         self.check(self.L.fhr_reconstruct_batch(self._h, len(sinos), arr, ctypes.byref(prm), _ptr(ws), n.value))
         if check_status:
             self.check(self.status(ws))
-        return xss, (prm.tile or 2)
+        return xss, (prm.tile or 2), prm.vw
 
     # ------------------------------------------------------------ expand
     def expand(self, xs, D, N, Nr, *, k0=0, k1=0, xh_dtype=F32, xh=None):

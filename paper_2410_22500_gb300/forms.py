@@ -148,10 +148,13 @@ def batched(n_problems: int = 40, iters: int = 100) -> None:
         x = (r < 0.4 * N).float()[..., None] * (0.5 + torch.rand((1, 1, K), device="cuda", generator=gen))
         sinos.append(ctx.project(x.contiguous(), N, Nv))
     Ns, Ks = [s[0] for s in shapes], [s[2] for s in shapes]
-    _, tile = ctx.reconstruct_batch(sinos, Ns, Ks, 4, autotune=True)
+    _, tile, vw = ctx.reconstruct_batch(sinos, Ns, Ks, 4, autotune=True)
     out = {}
-    t_batch = _timed(ctx, lambda: out.__setitem__("xb", ctx.reconstruct_batch(sinos, Ns, Ks, iters, tile=tile)[0]))
-    t_setup = _timed(ctx, lambda: ctx.reconstruct_batch(sinos, Ns, Ks, 0, tile=tile))
+    t_batch = _timed(ctx, lambda: out.__setitem__("xb", ctx.reconstruct_batch(sinos, Ns, Ks, iters, tile=tile,
+                                                                              vw=vw)[0]))
+    t_setup = _timed(ctx, lambda: ctx.reconstruct_batch(sinos, Ns, Ks, 0, tile=tile, vw=vw))
+    # the default tile shape, for comparison with the tuned one
+    t_default = _timed(ctx, lambda: ctx.reconstruct_batch(sinos, Ns, Ks, iters))
     ctx.reconstruct(sinos[0], Ns[0], 1, Ks[0], 2)
     per, xs = [], []
     for s, N, K in zip(sinos, Ns, Ks):
@@ -161,8 +164,9 @@ def batched(n_problems: int = 40, iters: int = 100) -> None:
     worst = max(float(((a - b).norm() / b.norm().clamp_min(1e-30)).item()) for a, b in zip(out["xb"], xs))
     vox = sum(N * N * K for N, _, K in shapes)
     t_seq = sum(per)
-    print(json.dumps({"case": "batched", "problems": n_problems, "iters": iters, "tile": tile,
+    print(json.dumps({"case": "batched", "problems": n_problems, "iters": iters, "tile": tile, "vw": vw,
                       "batched_ms": round(t_batch, 2), "batched_setup_ms": round(t_setup, 2),
+                      "batched_default_tile_ms": round(t_default, 2),
                       "per_problem_total_ms": round(t_seq, 2), "speedup": round(t_seq / t_batch, 3),
                       "voxel_channel_iters_per_s": vox * iters / (t_batch / 1e3),
                       "max_rel_diff_vs_per_problem": worst,

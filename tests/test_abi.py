@@ -61,8 +61,8 @@ int main(void) {
          offsetof(fhr_pipeline_params, host_io), offsetof(fhr_nmf_params, mlp_params), sizeof(fhr_mlp_dims));
   printf("%zu %zu %zu\n", offsetof(fhr_nmf_params, kmeans_samples), offsetof(fhr_nmf_params, kmeans_iters),
          offsetof(fhr_pipeline_params, recon));
-  printf("%zu %zu %zu %zu %zu\n", sizeof(fhr_problem), offsetof(fhr_problem, sino), offsetof(fhr_problem, sigma_x),
-         sizeof(fhr_batch_params), offsetof(fhr_batch_params, tile));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(fhr_problem), offsetof(fhr_problem, sino), offsetof(fhr_problem, sigma_x),
+         sizeof(fhr_batch_params), offsetof(fhr_batch_params, tile), offsetof(fhr_batch_params, vw));
   return 0;
 }
 ''')
@@ -78,7 +78,7 @@ int main(void) {
     assert km == [fhr.NmfParams.kmeans_samples.offset, fhr.NmfParams.kmeans_iters.offset,
                   fhr.PipelineParams.recon.offset]
     assert batch == [ctypes.sizeof(fhr.Problem), fhr.Problem.sino.offset, fhr.Problem.sigma_x.offset,
-                     ctypes.sizeof(fhr.BatchParams), fhr.BatchParams.tile.offset]
+                     ctypes.sizeof(fhr.BatchParams), fhr.BatchParams.tile.offset, fhr.BatchParams.vw.offset]
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -33,14 +33,15 @@ BATCH_2D = [(16, 24, 18, 1, 3), (24, 36, 30, 1, 2), (9, 13, 7, 1, 1), (20, 30, 1
 BATCH_3D = [(12, 18, 10, 3, 2), (16, 20, 14, 2, 3), (10, 15, 9, 4, 1)]
 
 
-def _run(fx, orc, probs, iters, momentum=False, p=1.2, tile=0, sigmas=False, x0=None):
+def _run(fx, orc, probs, iters, momentum=False, p=1.2, tile=0, vw=0, sigmas=False, x0=None):
     V = [_sino(orc, N, Nc, Nv, Nr, K, seed=100 + i) for i, (N, Nc, Nv, Nr, K) in enumerate(probs)]
     sg = None
     if sigmas:
         sg = [orc.mbir_sigmas(v.astype(np.float64).reshape(-1, K), K, Nc) for v, (N, Nc, Nv, Nr, K) in zip(V, probs)]
     xss = None if x0 is None else [_dev(x) for x in x0]
-    out, t = fx.reconstruct_batch([_dev(v) for v in V], [b[0] for b in probs], [b[4] for b in probs], iters,
-                                  Nr=[b[3] for b in probs], xss=xss, sigmas=sg, momentum=momentum, p=p, tile=tile)
+    out, t, _ = fx.reconstruct_batch([_dev(v) for v in V], [b[0] for b in probs], [b[4] for b in probs], iters,
+                                     Nr=[b[3] for b in probs], xss=xss, sigmas=sg, momentum=momentum, p=p, tile=tile,
+                                     vw=vw)
     return V, [o.cpu().numpy() for o in out], t
 
 
@@ -57,6 +58,17 @@ def test_batch_matches_single_and_oracle(fx, orc, probs, momentum):
         assert_close(g, ref, 1e-4)
 
 
+def test_wide_channel_vectors(fx, orc):
+    # 3-D problems whose Nr*K exceeds a block's 256 threads: 320 and 260 values (multiples
+    # of 4, so four values per thread), every tile width requested falls back to one that fits
+    probs = [(12, 18, 10, 64, 5), (10, 15, 9, 52, 5)]
+    iters = 5
+    V, got, _ = _run(fx, orc, probs, iters, momentum=True, vw=1)
+    for v, g, (N, Nc, Nv, Nr, K) in zip(V, got, probs):
+        single = fx.reconstruct(_dev(v), N, Nr, K, iters, momentum=True).cpu().numpy()
+        assert_close(g, single, 1e-6)
+
+
 def test_batch_explicit_sigmas_and_warm_start(fx, orc):
     probs = BATCH_2D[:3]
     rng = np.random.default_rng(9)
@@ -69,20 +81,23 @@ def test_batch_explicit_sigmas_and_warm_start(fx, orc):
         assert_close(g, ref, 1e-4)
 
 
-def test_tile_does_not_change_results(fx, orc):
-    # every pixel and ray runs the same arithmetic whatever the work-item size
-    _, a, _ = _run(fx, orc, BATCH_2D, 6, tile=1)
-    _, b, _ = _run(fx, orc, BATCH_2D, 6, tile=8)
-    for x, y in zip(a, b):
-        np.testing.assert_array_equal(x, y)
+@pytest.mark.parametrize("probs", [BATCH_2D, BATCH_3D], ids=["2d", "3d"])
+def test_tile_shape_does_not_change_results(fx, orc, probs):
+    # every channel of every pixel and ray is summed in the same order whatever the
+    # work-item size and the values per thread
+    _, a, _ = _run(fx, orc, probs, 6, tile=1)
+    for tile, vw in ((8, 0), (2, 2), (4, 1)):
+        _, b, _ = _run(fx, orc, probs, 6, tile=tile, vw=vw)
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
 
 
 def test_autotune_picks_a_candidate(fx, orc):
     V = [_sino(orc, N, Nc, Nv, Nr, K, seed=100 + i) for i, (N, Nc, Nv, Nr, K) in enumerate(BATCH_2D)]
     Ns, Ks = [b[0] for b in BATCH_2D], [b[4] for b in BATCH_2D]
-    tuned, tile = fx.reconstruct_batch([_dev(v) for v in V], Ns, Ks, 6, autotune=True)
-    assert tile in (1, 2, 4, 8, 16)
-    plain, _ = fx.reconstruct_batch([_dev(v) for v in V], Ns, Ks, 6, tile=2)
+    tuned, tile, vw = fx.reconstruct_batch([_dev(v) for v in V], Ns, Ks, 6, autotune=True)
+    assert tile in (1, 2, 4, 8, 16) and vw in (1, 2, 4)
+    plain, _, _ = fx.reconstruct_batch([_dev(v) for v in V], Ns, Ks, 6, tile=2)
     for x, y in zip(tuned, plain):
         np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
 
@@ -102,9 +117,9 @@ def test_autotune_leaves_volumes_alone(fx, orc):
     n = ctypes.c_size_t()
     fx.check(fx.L.fhr_reconstruct_batch_workspace_size(fx._h, 2, arr, ctypes.byref(prm), ctypes.byref(n)))
     ws = fx.workspace(n.value)
-    best = ctypes.c_int()
+    best, best_vw = ctypes.c_int(), ctypes.c_int()
     fx.check(fx.L.fhr_reconstruct_batch_autotune(fx._h, 2, arr, ctypes.byref(prm), fhr._ptr(ws), n.value,
-                                                 ctypes.byref(best)))
+                                                 ctypes.byref(best), ctypes.byref(best_vw)))
     assert fx.status(ws) == 0
     for x in xs:
         assert torch.all(x == 0.25)
@@ -132,9 +147,9 @@ def test_batch_rejects_bad_problems(fx, orc):
     with pytest.raises(fhr.FhrError) as e:   # K above the maximum
         fx.reconstruct_batch([a], [12], [9], 3)
     assert e.value.code == fhr.ERR_ARG
-    big = torch.zeros((10, 18, 264), device="cuda")   # Nr*K = 264 > 256 lanes
+    big = torch.zeros((10, 18, 259), device="cuda")   # Nr*K = 259: odd, so one value per thread > 256 lanes
     with pytest.raises(fhr.FhrError) as e:
-        fx.reconstruct_batch([big], [12], [8], 3, Nr=33)
+        fx.reconstruct_batch([big], [12], [7], 3, Nr=37)
     assert e.value.code == fhr.ERR_ARG
     with pytest.raises(fhr.FhrError) as e:
         fx.reconstruct_batch([a], [12], [2], 3, q=1.5)
