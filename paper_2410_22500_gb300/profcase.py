@@ -162,7 +162,7 @@ if __name__ == "__main__":
     elif case == "mbir_volume":
         mbir(3, N=256, Nr=256, K=6, Nv=120, Nc=256)
     elif case == "normalise_expand":
-        normalise_expand()
+        normalise_expand(int(sys.argv[2]) if len(sys.argv) > 2 else 8)
     elif case == "fmd":
         fmd()
     elif case == "mlp":
