@@ -72,6 +72,32 @@ def test_padded_row_stride_matches_oracle(fx, orc, dtype, ldP):
     np.testing.assert_allclose(obj.cpu().numpy(), objr, rtol=1e-4)
 
 
+def test_row_stride_does_not_change_results(fx):
+    # the 256^3 form's rows (1500 bf16 bins): stored with the pipeline's stride (1544, one
+    # bulk copy per 8-row tile) and with the plain one (1504, one copy per row), the pass
+    # does the same arithmetic on the same live bins, so D, W and the objective agree bit
+    # for bit; 98,305 rows leave a ragged last tile
+    import torch
+    from paper_2410_22500_gb300 import fhr, synth
+
+    assert fhr.nmf_row_stride(1500, fhr.BF16) == 1544
+    rng = np.random.default_rng(17)
+    Np, Nk, K = 98305, 1500, 6
+    g = torch.Generator(device="cuda")
+    g.manual_seed(17)
+    live = torch.rand((Np, Nk), device="cuda", generator=g).to(torch.bfloat16)
+    D0, W0 = synth.nmf_given_init(rng, Np, Nk, K)
+    out = []
+    for ldP in (1504, 1544):
+        P = torch.zeros((Np, ldP), dtype=torch.bfloat16, device="cuda")
+        P[:, :Nk] = live
+        D, W, obj = fx.decompose(P, Nk, K, 3, D=_dev(D0.astype(np.float32)), W=_dev(W0.astype(np.float32)))
+        out.append((D.cpu().numpy(), W.cpu().numpy(), obj.cpu().numpy()))
+        del P
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_tiny_2d_workload_final_objective(fx, orc):
     # the 32x32 / 60-view / Nk=128 / K=3 workload, 200 iterations: final objective within 1e-3
     from paper_2410_22500_gb300 import synth
