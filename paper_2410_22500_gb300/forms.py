@@ -109,7 +109,7 @@ def precision() -> None:
         ctx.check(ctx.status(ws))
         es = 2 if p_dtype == fhr.BF16 else 4
         n, pms = fams["nmf_pass"]
-        pass_bytes = g.Np * prm.nmf.ldP * es + 2 * g.Np * K_PRECISION * 4
+        pass_bytes = g.Np * pb.Nk * es + 2 * g.Np * K_PRECISION * 4   # the live bins (row padding not counted)
         vb = g.Nr * g.N * g.N * pb.Nk
         print(json.dumps({
             "case": "precision", "p_dtype": name, "workload": "256^3 volume, Nk=1500, 120 views, K=6, 100 counts/bin",
